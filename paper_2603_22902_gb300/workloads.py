@@ -1,0 +1,281 @@
+"""Seeded synthetic inputs: case parameters and initial fields.
+
+This module is the only code shared by the CUDA path's tests/benchmark and the
+CPU oracle.  It holds no lattice-Boltzmann arithmetic: it only lays out the
+geometry of the paper's test problems (Section 4: tanh order-parameter
+profiles of the film, the sessile drop, the compound drop and the pools) and
+chooses parameters.  Random draws use splitmix64 (Steele, Lea, Flood 2014),
+uniform doubles as (x >> 11) * 2**-53.
+
+Coordinates: cell (i, j) has its centre at (i + 1/2, j + 1/2); a half-way wall
+on the y-min side sits at y = 0.
+"""
+from __future__ import annotations
+
+import copy
+import dataclasses
+import math
+from typing import List
+
+import numpy as np
+
+PERIODIC, WALL, OUTFLOW = 0, 1, 2
+ADIABATIC, DIRICHLET = 0, 1
+XMIN, XMAX, YMIN, YMAX = 0, 1, 2, 3
+
+
+@dataclasses.dataclass
+class Case:
+    """Parameters and initial fields of one problem."""
+
+    name: str
+    nx: int
+    ny: int
+    N: int
+    phases: List[dict]          # rho_l, rho_s, mu_l, mu_s, lam_l, lam_s, cp_l, cp_s, latent
+    sigma: np.ndarray           # [N, N]
+    eps: float = 4.0
+    mobility: float = 0.02
+    T_sol: float = 0.0
+    T_liq: float = 0.0
+    rho_ref: float = 1.0
+    cp_ref: float = 1.0
+    u_solid: tuple = (0.0, 0.0)
+    accel: tuple = (0.0, 0.0)
+    bc: tuple = (PERIODIC, PERIODIC, PERIODIC, PERIODIC)
+    tbc: tuple = (ADIABATIC, ADIABATIC, ADIABATIC, ADIABATIC)
+    T_wall: tuple = (0.0, 0.0, 0.0, 0.0)
+    wet_cos: np.ndarray = None  # [4, N, N], antisymmetric per side
+    phi: np.ndarray = None      # [N, ny, nx]
+    T: np.ndarray = None        # [ny, nx]
+    ux: np.ndarray = None
+    uy: np.ndarray = None
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    def __post_init__(self):
+        self.sigma = np.asarray(self.sigma, dtype=np.float64)
+        if self.wet_cos is None:
+            self.wet_cos = np.zeros((4, self.N, self.N))
+        if self.T is None:
+            self.T = np.zeros((self.ny, self.nx))
+        if self.ux is None:
+            self.ux = np.zeros((self.ny, self.nx))
+        if self.uy is None:
+            self.uy = np.zeros((self.ny, self.nx))
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny
+
+    def copy(self) -> "Case":
+        return copy.deepcopy(self)
+
+
+# --------------------------------------------------------------------------
+# random numbers
+# --------------------------------------------------------------------------
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """First n outputs of splitmix64 started at `seed` (uint64)."""
+    with np.errstate(over="ignore"):
+        k = np.arange(1, n + 1, dtype=np.uint64)
+        z = (np.uint64(seed & _M64) + k * np.uint64(0x9E3779B97F4A7C15))
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    u = (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return lo + (hi - lo) * u
+
+
+# --------------------------------------------------------------------------
+# building blocks
+# --------------------------------------------------------------------------
+
+def phase(rho_l=1.0, rho_s=None, mu_l=0.1, mu_s=None, lam_l=0.1, lam_s=None,
+          cp_l=1.0, cp_s=None, latent=0.0) -> dict:
+    return dict(rho_l=rho_l, rho_s=rho_l if rho_s is None else rho_s,
+                mu_l=mu_l, mu_s=mu_l if mu_s is None else mu_s,
+                lam_l=lam_l, lam_s=lam_l if lam_s is None else lam_s,
+                cp_l=cp_l, cp_s=cp_l if cp_s is None else cp_s, latent=latent)
+
+
+def tanh_step(d, eps):
+    """1/2 + 1/2 tanh(d / (eps/2)): 1 where d > 0 (Section 4 initial profiles)."""
+    return 0.5 + 0.5 * np.tanh(d / (eps / 2.0))
+
+
+def grid(nx, ny):
+    x = np.arange(nx) + 0.5
+    y = np.arange(ny) + 0.5
+    return np.meshgrid(x, y)  # X[ny, nx], Y[ny, nx]
+
+
+def sigma_matrix(N, pairs):
+    s = np.zeros((N, N))
+    for (p, q), v in pairs.items():
+        s[p, q] = s[q, p] = v
+    return s
+
+
+def wetting(N, side_angles):
+    """wet_cos[4, N, N] from {side: {(p, q): theta_deg}} (cos antisymmetric)."""
+    w = np.zeros((4, N, N))
+    for side, pairs in side_angles.items():
+        for (p, q), th in pairs.items():
+            c = math.cos(math.radians(th))
+            w[side, p, q] = c
+            w[side, q, p] = -c
+    return w
+
+
+def latent_from_stefan(ste: float, cp_s: float = 1.0, dT_ref: float = 1.0) -> float:
+    """Ste = c_p,s (T_m - T_w) / L with a fixed reference difference T_m - T_w = dT_ref."""
+    return cp_s * dT_ref / ste
+
+
+# --------------------------------------------------------------------------
+# the paper's problems (Section 4) and the small cases of the tests
+# --------------------------------------------------------------------------
+
+def film(nx=16, ny=256, h0=128.0, ste=0.1, rho_ratio=0.9, T_wall=-1.0, T0=0.0,
+         lam=0.1, mu=0.1, sigma=1e-3, eps=4.0, mobility=0.02, rho_gas=1.0) -> Case:
+    """Film freezing (Section 4.1): liquid 0 < y < h0 under gas, cold bottom wall,
+    outflow top, x periodic."""
+    X, Y = grid(nx, ny)
+    phi1 = tanh_step(h0 - Y, eps)
+    phi = np.stack([phi1, 1.0 - phi1])
+    phases = [phase(rho_l=1.0, rho_s=rho_ratio, mu_l=mu, lam_l=lam, latent=latent_from_stefan(ste)),
+              phase(rho_l=rho_gas, mu_l=mu * rho_gas, lam_l=lam)]
+    return Case(name=f"film_{nx}x{ny}", nx=nx, ny=ny, N=2, phases=phases,
+                sigma=sigma_matrix(2, {(0, 1): sigma}), eps=eps, mobility=mobility,
+                bc=(PERIODIC, PERIODIC, WALL, OUTFLOW), tbc=(ADIABATIC, ADIABATIC, DIRICHLET, ADIABATIC),
+                T_wall=(0.0, 0.0, T_wall, 0.0), phi=phi, T=np.full((ny, nx), T0),
+                meta=dict(h0=h0, ste=ste, rho_ratio=rho_ratio, T_wall=T_wall))
+
+
+def sessile_drop(n=512, R=100.0, ste=0.1, rho_ratio=0.9, theta=90.0, T_wall=-1.0, T0=1.0,
+                 rho_gas=0.01, mu_l=0.02, mu_gas=0.002, lam_l=0.1, lam_gas=0.01, cp_gas=100.0,
+                 sigma=1e-3, eps=4.0, mobility=0.02, ny=None) -> Case:
+    """Single droplet on a cold wall (Section 4.2): drop of radius R centred on the
+    bottom wall, gas around it, x periodic, bottom Dirichlet + wetting, top adiabatic wall.
+
+    Unstated parameters: the drop starts superheated at T0 = 1 (the paper's film
+    setting), and the gas heat capacity makes rho_g c_g equal to rho_l c_l, because the
+    total-enthalpy LBE with one rho_ref c_p,ref is unstable where rho c_p is far below it."""
+    nx, ny = n, (ny or n)
+    X, Y = grid(nx, ny)
+    r = np.sqrt((X - nx / 2.0) ** 2 + Y ** 2)
+    phi1 = tanh_step(R - r, eps)
+    phi = np.stack([phi1, 1.0 - phi1])
+    phases = [phase(rho_l=1.0, rho_s=rho_ratio, mu_l=mu_l, lam_l=lam_l, latent=latent_from_stefan(ste)),
+              phase(rho_l=rho_gas, mu_l=mu_gas, lam_l=lam_gas, cp_l=cp_gas)]
+    return Case(name=f"sessile_drop_{nx}x{ny}", nx=nx, ny=ny, N=2, phases=phases,
+                sigma=sigma_matrix(2, {(0, 1): sigma}), eps=eps, mobility=mobility,
+                bc=(PERIODIC, PERIODIC, WALL, WALL), tbc=(ADIABATIC, ADIABATIC, DIRICHLET, ADIABATIC),
+                T_wall=(0.0, 0.0, T_wall, 0.0), wet_cos=wetting(2, {YMIN: {(0, 1): theta}}),
+                phi=phi, T=np.full((ny, nx), T0),
+                meta=dict(R=R, ste=ste, rho_ratio=rho_ratio, theta=theta, T_wall=T_wall))
+
+
+def compound_drop(n=1024, R_core=80.0, R_shell=160.0, ste=0.2, seed=3, noise=1e-3,
+                  T_wall=-1.0, T0=1.0, sigma12=1e-3, sigma23=1.5e-3, sigma13=3e-3,
+                  eps=4.0, mobility=0.02, ny=None) -> Case:
+    """Encapsulated compound drop (Section 4.3, Table 3): liquid core (phase 1) inside a
+    liquid shell (phase 2) on a cold wall in gas (phase 3)."""
+    nx, ny = n, (ny or n)
+    X, Y = grid(nx, ny)
+    r = np.sqrt((X - nx / 2.0) ** 2 + Y ** 2)
+    phi1 = tanh_step(R_core - r, eps)
+    phi2 = (1.0 - phi1) * tanh_step(R_shell - r, eps)
+    if noise:
+        xi = uniform(seed, 2 * nx * ny, -noise, noise).reshape(2, ny, nx)
+        phi1 = np.clip(phi1 + xi[0], 0.0, 1.0)
+        phi2 = np.clip(phi2 + xi[1], 0.0, 1.0)
+        over = phi1 + phi2
+        scale = np.where(over > 1.0, 1.0 / over, 1.0)
+        phi1, phi2 = phi1 * scale, phi2 * scale
+    phi3 = 1.0 - phi1 - phi2
+    phi = np.stack([phi1, phi2, np.maximum(phi3, 0.0)])
+    lam1 = 0.1
+    phases = [phase(rho_l=1.0, rho_s=1.1, mu_l=0.02, lam_l=lam1, latent=latent_from_stefan(ste)),
+              phase(rho_l=0.9, rho_s=0.81, mu_l=0.02, lam_l=2.7 * lam1, latent=latent_from_stefan(ste)),
+              phase(rho_l=0.01, mu_l=0.002, lam_l=0.1 * lam1, cp_l=100.0)]
+    sig = sigma_matrix(3, {(0, 1): sigma12, (1, 2): sigma23, (0, 2): sigma13})
+    return Case(name=f"compound_drop_{nx}x{ny}", nx=nx, ny=ny, N=3, phases=phases, sigma=sig,
+                eps=eps, mobility=mobility,
+                bc=(PERIODIC, PERIODIC, WALL, WALL), tbc=(ADIABATIC, ADIABATIC, DIRICHLET, ADIABATIC),
+                T_wall=(0.0, 0.0, T_wall, 0.0), phi=phi, T=np.full((ny, nx), T0),
+                meta=dict(R_core=R_core, R_shell=R_shell, ste=ste, seed=seed))
+
+
+def periodic_drop(n=64, R=16.0, sigma=1e-3, rho_ratio=1.0, mu=0.1, eps=4.0, mobility=0.02,
+                  N=2, rho_gas=1.0, ny=None, cx=None, cy=None) -> Case:
+    """A drop in a fully periodic box, no phase change (Laplace-law problem)."""
+    nx, ny = n, (ny or n)
+    X, Y = grid(nx, ny)
+    cx = nx / 2.0 if cx is None else cx
+    cy = ny / 2.0 if cy is None else cy
+    r = np.sqrt((X - cx) ** 2 + (Y - cy) ** 2)
+    phi1 = tanh_step(R - r, eps)
+    phis = [phi1, 1.0 - phi1] + [np.zeros_like(phi1)] * (N - 2)
+    phases = [phase(rho_l=1.0, mu_l=mu), phase(rho_l=rho_gas, mu_l=mu * rho_gas)]
+    phases += [phase(rho_l=1.0, mu_l=mu) for _ in range(N - 2)]
+    sig = np.full((N, N), sigma)
+    np.fill_diagonal(sig, 0.0)
+    return Case(name=f"periodic_drop_{nx}x{ny}", nx=nx, ny=ny, N=N, phases=phases, sigma=sig,
+                eps=eps, mobility=mobility, phi=np.stack(phis), meta=dict(R=R, sigma=sigma))
+
+
+def flat_interface(nx=4, ny=64, h0=None, sigma=1e-3, eps=4.0, mobility=0.02) -> Case:
+    """Two flat interfaces in a periodic column (an exact tanh equilibrium of the AC equation)."""
+    X, Y = grid(nx, ny)
+    h0 = ny / 4.0 if h0 is None else h0
+    phi1 = tanh_step(h0 - np.abs(Y - ny / 2.0), eps)
+    phases = [phase(), phase()]
+    return Case(name=f"flat_{nx}x{ny}", nx=nx, ny=ny, N=2, phases=phases,
+                sigma=sigma_matrix(2, {(0, 1): sigma}), eps=eps, mobility=mobility,
+                phi=np.stack([phi1, 1.0 - phi1]), meta=dict(h0=h0))
+
+
+def lateral_pool(n=64, eps=4.0, sigma=0.01, T_wall=-1.0, T0=0.0, ste=0.2, freeze=True,
+                 rho_ratio1=1.0, rho_ratio2=1.0, mobility=0.02) -> Case:
+    """Two laterally placed liquids under gas (Section 4.1, Fig. 4 initial fields), walls
+    on all sides.  With freeze=False the bottom wall is warm (no phase change)."""
+    nx = ny = n
+    X, Y = grid(nx, ny)
+    L = float(n)
+    lower = tanh_step(L / 2.0 - Y, eps)
+    phi1 = tanh_step(L / 2.0 - X, eps) * lower
+    phi2 = tanh_step(X - L / 2.0, eps) * lower
+    phi3 = 1.0 - phi1 - phi2
+    lat = latent_from_stefan(ste)
+    phases = [phase(rho_l=1.0, rho_s=rho_ratio1, mu_l=0.05, latent=lat),
+              phase(rho_l=1.0, rho_s=rho_ratio2, mu_l=0.05, latent=lat),
+              phase(rho_l=1.0, mu_l=0.05)]
+    sig = np.full((3, 3), sigma)
+    np.fill_diagonal(sig, 0.0)
+    return Case(name=f"lateral_pool_{n}", nx=nx, ny=ny, N=3, phases=phases, sigma=sig, eps=eps,
+                mobility=mobility, bc=(WALL, WALL, WALL, WALL),
+                tbc=(ADIABATIC, ADIABATIC, DIRICHLET if freeze else ADIABATIC, ADIABATIC),
+                T_wall=(0.0, 0.0, T_wall, 0.0), phi=np.stack([phi1, phi2, phi3]),
+                T=np.full((ny, nx), T0))
+
+
+def perturbed(case: Case, seed: int, amp_u: float = 1e-3, amp_T: float = 0.0) -> Case:
+    """Same case with seeded uniform noise on the initial velocity (and temperature)."""
+    c = case.copy()
+    n = c.nx * c.ny
+    r = uniform(seed, 3 * n, -1.0, 1.0).reshape(3, c.ny, c.nx)
+    c.ux = c.ux + amp_u * r[0]
+    c.uy = c.uy + amp_u * r[1]
+    if amp_T:
+        c.T = c.T + amp_T * r[2]
+    c.name += f"_perturbed{seed}"
+    return c

@@ -1,0 +1,132 @@
+"""Invariants of the coupled scheme that pin the oracle (Sections 2-3):
+
+* the t = 0 populations carry the moments of the equilibria defined in Section 3;
+* per-phase volume sum_x phi_p is conserved when nothing freezes (mdot = 0);
+* sum_p phi_p = 1 is kept exactly when there is no flow;
+* reduction consistency: an absent phase stays absent and N = 3 with phi_3 = 0
+  reproduces the N = 2 run bit for bit (Section 2);
+* N = 2 reproduces the textbook two-phase conservative Allen-Cahn model with the
+  standard free energy (R = 4 phi (1 - phi) n / eps, mu = beta g' - kappa lap phi);
+* mirror and 90-degree rotation symmetry of the discrete operators.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_22902_gb300 import workloads as W
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+
+
+def test_initial_populations_carry_equilibrium_moments():
+    c = W.perturbed(W.sessile_drop(n=24, R=8.0, T0=0.5), seed=11, amp_u=2e-3, amp_T=0.3)
+    o = oracle.Oracle(c)
+    f, g, h = o.populations()
+    F = o.fields()
+    rhoH0 = np.array([[oracle.inverse_map(c, c.phi[:, j, i], c.T[j, i]) for i in range(c.nx)]
+                      for j in range(c.ny)])
+    # zeroth moments: sum f = 0 (p = 0), sum g_p = phi_p, sum h = rho H
+    assert np.abs(f.sum(0)).max() < 1e-15
+    assert np.abs(g.sum(1) - c.phi).max() < 1e-15
+    assert np.abs(h.sum(0) - rhoH0).max() < 1e-14
+    # first moments: rho u, phi_p u, rho c_p T u
+    rho = F["rho"]
+    jx, jy = np.tensordot(CX, f, 1), np.tensordot(CY, f, 1)
+    assert np.abs(jx - rho * c.ux).max() < 1e-16 and np.abs(jy - rho * c.uy).max() < 1e-16
+    gxm = np.einsum("i,pijk->pjk", CX, g)
+    assert np.abs(gxm - c.phi * c.ux).max() < 1e-16
+    hx = np.tensordot(CX, h, 1)
+    cp = np.ones_like(rho) * np.where(c.phi[0] > -1, 1.0, 1.0)
+    cp = (1 - F["fl"]) * (c.phi[0] * 1.0 + c.phi[1] * c.phases[1]["cp_s"]) + F["fl"] * (
+        c.phi[0] * 1.0 + c.phi[1] * c.phases[1]["cp_l"])
+    assert np.abs(hx - rho * cp * F["T"] * c.ux).max() < 1e-13
+    # second moment of f: p/c_s^2 * c_s^2 I + rho u u at p = 0
+    pxx = np.tensordot(CX * CX, f, 1)
+    assert np.abs(pxx - rho * c.ux * c.ux).max() < 1e-16
+
+
+def test_phase_volume_conserved_without_freezing():
+    c = W.periodic_drop(n=32, R=9.0, rho_gas=0.1, cy=12.0)
+    c.bc = (W.PERIODIC, W.PERIODIC, W.WALL, W.WALL)
+    c = W.perturbed(c, seed=5, amp_u=1e-3)
+    o = oracle.Oracle(c)
+    m0 = o.fields()["phi"].sum(axis=(1, 2))
+    o.step(400)
+    m1 = o.fields()["phi"].sum(axis=(1, 2))
+    assert np.abs(m1 / m0 - 1.0).max() < 1e-12
+
+
+def test_sum_of_order_parameters_exact_without_flow():
+    c = W.periodic_drop(n=24, R=6.0, N=3, sigma=0.0)
+    c.phi[2] = 0.5 * c.phi[1]
+    c.phi[1] = 0.5 * c.phi[1]
+    c.bc = (W.WALL, W.WALL, W.WALL, W.WALL)
+    o = oracle.Oracle(c).step(300)
+    F = o.fields()
+    assert np.abs(F["phi"].sum(0) - 1.0).max() < 1e-13
+    assert np.abs(F["ux"]).max() == 0.0
+
+
+def test_absent_phase_reduction_is_exact():
+    c2 = W.sessile_drop(n=24, R=7.0, T_wall=-1.0, theta=70.0)
+    c3 = c2.copy()
+    c3.N = 3
+    c3.phi = np.concatenate([c2.phi, np.zeros((1, c2.ny, c2.nx))])
+    c3.phases = c2.phases + [W.phase(rho_l=0.5, rho_s=0.4, latent=3.0)]
+    s = np.zeros((3, 3))
+    s[:2, :2] = c2.sigma
+    s[0, 2] = s[2, 0] = 2e-3
+    s[1, 2] = s[2, 1] = 1e-3
+    c3.sigma = s
+    wc = np.zeros((4, 3, 3))
+    wc[:, :2, :2] = c2.wet_cos
+    c3.wet_cos = wc
+    o2, o3 = oracle.Oracle(c2).step(150), oracle.Oracle(c3).step(150)
+    F2, F3 = o2.fields(), o3.fields()
+    assert np.all(F3["phi"][2] == 0.0)
+    for k in ("T", "H", "fl", "ux", "uy", "p", "rho"):
+        assert np.array_equal(F2[k], F3[k]), k
+    assert np.array_equal(F2["phi"], F3["phi"][:2])
+    g3 = o3.populations()[1][2]
+    assert np.all(g3 == 0.0)
+
+
+def test_two_phase_reduces_to_textbook_model():
+    # The pairwise terms equal the textbook ones while phi_1 + phi_2 = 1 holds exactly:
+    # at t = 0 (u and p carry F_s / 2 and the F_0 term) and for phi after one step
+    # (phi(x) gathers the neighbours' post-collision g, which carry R_p).  Later the
+    # weakly compressible flow makes sum_p phi_p drift from 1 and the two models part.
+    c = W.periodic_drop(n=32, R=9.0, rho_gas=0.2, sigma=2e-3, cx=15.3, cy=17.1)
+    a, b = oracle.Oracle(c), oracle.Oracle(c, two_phase_textbook=True)
+    A, B = a.fields(), b.fields()
+    for k in ("ux", "uy", "p"):
+        assert np.abs(A[k]).max() > 1e-6, k
+        assert np.abs(A[k] - B[k]).max() < 1e-13 * np.abs(A[k]).max(), k
+    A, B = a.step(1).fields(), b.step(1).fields()
+    assert np.abs(A["phi"] - B["phi"]).max() < 1e-15
+
+
+def test_mirror_symmetry():
+    c = W.sessile_drop(n=32, R=9.0, theta=60.0)  # symmetric about x = nx/2
+    F = oracle.Oracle(c).step(120).fields()
+    assert np.abs(F["phi"] - F["phi"][:, :, ::-1]).max() < 1e-13
+    assert np.abs(F["T"] - F["T"][:, ::-1]).max() < 1e-13
+    assert np.abs(F["ux"] + F["ux"][:, ::-1]).max() < 1e-15
+    assert np.abs(F["uy"] - F["uy"][:, ::-1]).max() < 1e-15
+
+
+def test_rotation_symmetry():
+    c = W.perturbed(W.periodic_drop(n=20, R=5.0, rho_gas=0.3, cx=8.0, cy=11.0), seed=9, amp_u=1e-3)
+    r = c.copy()
+    r.phi = np.rot90(c.phi, 1, axes=(1, 2)).copy()
+    # np.rot90 over (y, x) with y pointing up turns the plane clockwise by 90 degrees:
+    # (x, y) -> (y, -x), so (ux, uy) -> (uy, -ux)
+    r.ux = np.rot90(c.uy).copy()
+    r.uy = np.rot90(-c.ux).copy()
+    Fa = oracle.Oracle(c).step(100).fields()
+    Fb = oracle.Oracle(r).step(100).fields()
+    assert np.abs(np.rot90(Fa["phi"], 1, axes=(1, 2)) - Fb["phi"]).max() < 1e-13
+    assert np.abs(np.rot90(Fa["p"]) - Fb["p"]).max() < 1e-15
+    assert np.abs(np.rot90(Fa["uy"]) - Fb["ux"]).max() < 1e-15
+    assert np.abs(np.rot90(-Fa["ux"]) - Fb["uy"]).max() < 1e-15
