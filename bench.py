@@ -1,0 +1,322 @@
+"""Benchmark of the fused coupled LB step on GB300 (one JSON line on stdout).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+                    [--workload NAME] [--precision fp64]
+
+Workload (default): the single sessile droplet freezing on a cold wall, 512 x 512,
+N = 2, FP64 (the second problem of Section 4; inputs synthetic, built by
+paper_2603_22902_gb300.workloads).  A step is one fused time step over the lattice.
+Timing: W untimed warm-up steps, then K steps, each timed with CUDA events on the
+launching stream and preceded by an untimed L2 flush (a 256 MiB write), bracketed by
+a barrier + device synchronise; the max over ranks is reported.  With N > 1 every rank
+runs its own replica of the workload (replicas only: the single-lattice step has no
+multi-GPU path here), so the scaling is weak.
+
+The reference arm (--impl reference) times the CPU oracle (oracle/) as it stands on
+the host cores, one oracle time step of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled-step MLUPS and % HBM roofline at 1 GB300; reduced-precision vs FP64 at stated error"
+# Algorithmic bytes per lattice update of the fused step: every population read and
+# written once, every lagged plane read and written once, 8 bytes each (FP64):
+# 2 * 8 * (9 (N + 2) + 3 + 2 N).
+def bytes_per_lu(N: int, elem: int = 8) -> int:
+    return 2 * elem * (9 * (N + 2) + 3 + 2 * N)
+
+
+# FP64 operations per lattice update of the fused step kernel (collision path), counted
+# from the SASS instruction mix with ncu (DFMA = 2, DADD/DMUL = 1); see the profile notes.
+FP64_FLOP_PER_LU = {2: None, 3: None, 4: None}
+# FP64 peak of a GB300 from unit counts: 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def make_case(name):
+    from paper_2603_22902_gb300 import workloads as W
+    if name == "sessile_drop_512":
+        return W.sessile_drop()
+    if name == "film_16x256":
+        return W.film()
+    if name == "compound_drop_1024":
+        return W.compound_drop()
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    """Max of a float over all ranks (identity for one process)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_oracle(case, steps, budget_s=20.0):
+    """The CPU oracle as it stands: oracle time steps of the case, single thread."""
+    import oracle
+    o = oracle.Oracle(case)
+    o.step(1)  # warm (page-in, caches)
+    done, t0 = 0, time.perf_counter()
+    while done < steps:
+        o.step(1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return case.cells * done / dt / 1e6, done, dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    case = make_case(args.workload)
+    mlups, done, dt = time_oracle(case, args.steps + args.warmup, budget_s=args.ref_budget)
+    cores = 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": done, "warmup": 1, "ms_per_step": round(1e3 * dt / done, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "N": case.N},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{done} oracle steps of {case.name} (of {args.steps + args.warmup} requested; "
+                                   f"{args.ref_budget:.0f} s budget), one host thread"},
+        "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_2603_22902_gb300 import build as B
+    if rank == 0:
+        B.build()
+    barrier(world)
+    from paper_2603_22902_gb300 import lbm
+
+    case = make_case(args.workload)
+    N = case.N
+    stream = torch.cuda.current_stream()
+    s = lbm.Solver(case, precision=args.precision, tile=tuple(args.tile) if args.tile else None)
+    s.set_fields()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        s.step(1)
+    torch.cuda.synchronize()
+    barrier(world)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                     # untimed: evict L2 between timed steps
+        starts[k].record(stream)
+        s.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier(world)
+    clk = clocks.stop()
+    per_step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    t_ms = sum(per_step_ms)
+    t_ms_max = reduce_max(t_ms, world)
+    diag = s.diagnostics()
+    if diag["nonfinite"]:
+        raise SystemExit("non-finite state during the benchmark")
+
+    cells = case.cells
+    value = world * cells * args.steps / (t_ms_max * 1e-3) / 1e6          # MLUPS, all ranks
+    mlups_rank = cells * args.steps / (t_ms * 1e-3) / 1e6
+    hbm_peak, peak_kind = load_peaks()
+    bpl = bytes_per_lu(N)
+    gbs = bpl * mlups_rank * 1e6 / 1e9
+    roof_hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(gbs / hbm_peak, 4), "traffic": args.traffic,
+                "peak_kind": peak_kind, "bytes_per_lu": bpl}
+    roofline = roof_hbm
+    flop = FP64_FLOP_PER_LU.get(N)
+    alu = None
+    if flop:
+        tf = flop * mlups_rank * 1e6 / 1e12
+        alu = {"bound": "alu", "achieved": round(tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+               "frac": round(tf / FP64_PEAK_TFLOPS, 4), "traffic": args.traffic, "flop_per_lu": flop,
+               "peak_kind": "derived from unit counts and max clock"}
+        if alu["frac"] > roof_hbm["frac"]:
+            roofline = dict(alu)
+            roofline["hbm"] = {k: roof_hbm[k] for k in ("achieved", "peak", "unit", "frac")}
+
+    # ---- end to end through the C ABI with host buffers ------------------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+        h_in = [pin(case.phi), pin(case.T), pin(case.ux), pin(case.uy)]
+        h_out = [torch.empty((N, case.ny, case.nx), dtype=torch.float64).pin_memory()] + \
+                [torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory() for _ in range(6)]
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        lbm.lbm_set_fields(s.h, h_in[0], h_in[1], h_in[2], h_in[3], lbm.LBM_HOST)
+        lbm.lbm_step(s.h, args.e2e_steps)
+        lbm.lbm_get_fields(s.h, *h_out, lbm.LBM_HOST)
+        torch.cuda.synchronize()
+        dt = reduce_max(time.perf_counter() - t0, world)
+        h2d = sum(t.numel() * 8 for t in h_in)
+        d2h = sum(t.numel() * 8 for t in h_out)
+        e2e = {"value": round(world * cells * args.e2e_steps / dt / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": int(h2d / args.e2e_steps), "d2h_bytes_per_step": int(d2h / args.e2e_steps),
+               "steps_per_call": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups_cpu, done, dt = time_oracle(case, 10 ** 6, budget_s=args.cpu_budget)
+        cpu = {"value": round(mlups_cpu, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{done} oracle time steps of {case.name} ({dt:.1f} s), one host thread"}
+
+    s.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms_max / args.steps, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp16s": "f16-storage/f32", "bf16s": "bf16-storage/f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "N": N, "precision": args.precision,
+                       "l2": "flushed (256 MiB write) before every timed step", "timing": "CUDA events per step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clk, "wall_s_timed_loop": round(t_wall, 4),
+        }
+        if alu is not None and roofline is roof_hbm:
+            line["roofline_alu"] = alu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="sessile_drop_512")
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--tile", type=int, nargs=2, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=120.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    return run_reference(args) if args.impl == "reference" else run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) coupled lattice Boltzmann solver for
+ * N-phase flows with liquid-solid phase change.
+ *
+ * Method: Huang, Zhan, Chai, Huang, Liu, "A diffuse-interface model for N-phase
+ * flows with liquid-solid phase change", arXiv 2603.22902.  Section 2 defines the
+ * model (mixture rule eq. 2, continuity with mass source, enthalpy equation and
+ * the enthalpy -> (f_l, T) map eq. H, N-phase conservative Allen-Cahn equation
+ * with the pairwise source R_p, reduction-consistent free energy, chemical
+ * potentials and the surface force F_s); Section 3 the three coupled lattice
+ * Boltzmann equations (pressure-based flow LBE with source S and penalty force,
+ * total-enthalpy LBE, N phase-field LBEs) on a D2Q9 lattice, c_s^2 = 1/3,
+ * dx = dt = 1.
+ *
+ * Conventions
+ *  - Every call returns an int status: LBM_OK (0) or a negative LBM_E* code.
+ *    lbm_last_error() returns a message for the last failing call on a handle.
+ *  - Fields are row-major [ny][nx] float64 (x fastest), whatever the internal
+ *    precision; phi is N such planes, contiguous ([N][ny][nx]).
+ *  - where = LBM_HOST: pointers are host memory (pinned or pageable); the call
+ *    copies and returns when the data is in place.  where = LBM_DEVICE: pointers
+ *    are device memory of the handle's device; the work is queued on the handle's
+ *    stream and the call returns without synchronising.
+ *  - The handle owns all device memory it allocates; the caller owns every buffer
+ *    it passes.  Calls on one handle are not thread-safe; work is stream-ordered.
+ *  - No CPU fallback: without a CUDA device every call that needs one fails with
+ *    LBM_ECUDA.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_MAXN 4
+
+/* status codes */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)    /* invalid argument or parameter set */
+#define LBM_ENOMEM (-2)    /* device or host allocation failed */
+#define LBM_ECUDA (-3)     /* CUDA runtime error (no device, launch failure, ...) */
+#define LBM_EUNSTABLE (-4) /* a non-finite value was found by the diagnostics */
+#define LBM_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define LBM_ESTATE (-6)    /* call out of order (e.g. step before set_fields) */
+
+/* boundary kinds per side; sides are 0 = x-min, 1 = x-max, 2 = y-min, 3 = y-max */
+#define LBM_BC_PERIODIC 0 /* both sides of an axis must be periodic, or neither */
+#define LBM_BC_WALL 1     /* half-way bounce-back, no-slip, wetting ghost for phi */
+#define LBM_BC_OUTFLOW 2  /* y sides only: incoming populations copied along the boundary row */
+#define LBM_T_ADIABATIC 0
+#define LBM_T_DIRICHLET 1 /* y-side walls only: non-equilibrium extrapolation (Section 4.1) */
+
+/* arithmetic / storage precision of the populations */
+#define LBM_FP64 0  /* FP64 storage and arithmetic (the parity path) */
+#define LBM_FP32 1  /* FP32 storage and arithmetic */
+#define LBM_FP16S 2 /* FP16 storage of shifted populations, FP32 arithmetic */
+#define LBM_BF16S 3 /* BF16 storage of shifted populations, FP32 arithmetic */
+
+#define LBM_HOST 0
+#define LBM_DEVICE 1
+
+typedef struct lbm_handle lbm_handle;
+
+typedef struct {
+    int nx, ny; /* lattice size, >= 3 each */
+} lbm_grid;
+
+/* Liquid and solid properties of one phase (eq. 2: density, viscosity, thermal
+ * conductivity, heat capacity) and its specific latent heat (Section 2, H = C_p T +
+ * L f_l); latent = 0 marks a phase that never changes phase (ambient, impurities). */
+typedef struct {
+    double rho_l, rho_s;
+    double mu_l, mu_s;
+    double lambda_l, lambda_s;
+    double cp_l, cp_s;
+    double latent;
+} lbm_phase;
+
+/* Thermal and body-force parameters.  T_sol <= T_liq are the solidus and liquidus
+ * temperatures of eq. H; rho_ref and cp_ref the reference density and heat capacity
+ * of the enthalpy LBE (Section 3; cp_ref = 0 selects 2 c_s c_l / (c_s + c_l) of
+ * phase 0); u_solid the solid velocity u_s of the penalty force; accel a body
+ * acceleration (the body force G = rho accel). */
+typedef struct {
+    double T_sol, T_liq;
+    double rho_ref, cp_ref;
+    double u_solid[2];
+    double accel[2];
+} lbm_thermal;
+
+/* Boundary description.  wet_cos[side][p*LBM_MAXN+q] = cos(theta_pq) of the wall on
+ * that side (antisymmetric in p, q; 0 = neutral wetting); it enters the ghost value
+ * of phi_p beyond the wall: phi_p + (4/eps) sum_q cos(theta_pq) phi_p phi_q. */
+typedef struct {
+    int kind[4];
+    int tkind[4];
+    double T_wall[4];
+    double wet_cos[4][LBM_MAXN * LBM_MAXN];
+} lbm_bc;
+
+/* Numerical parameters: interface width eps and mobility M (Section 3:
+ * M = c_s^2 (tau_g - 1/2)); pairwise surface tensions sigma[p*LBM_MAXN+q] (symmetric,
+ * zero diagonal; beta_pq = 3 sigma_pq / eps, k_pq = -3 eps sigma_pq / 4, Section 2);
+ * precision = LBM_FP64 / LBM_FP32 / LBM_FP16S / LBM_BF16S; diag_every = K > 0 makes
+ * lbm_step run the non-finite check every K steps (0 = only when asked). */
+typedef struct {
+    double eps, mobility;
+    double sigma[LBM_MAXN * LBM_MAXN];
+    int precision;
+    int diag_every;
+} lbm_numerics;
+
+/* Diagnostics of the current state: per-phase volume sum_x phi_p, per-phase solid
+ * volume sum_x f_s phi_p, max_x |sum_p phi_p - 1|, count of non-finite cells. */
+typedef struct {
+    double mass[LBM_MAXN];
+    double solid[LBM_MAXN];
+    double max_sum_dev;
+    long long nonfinite;
+    long long steps;
+} lbm_diag;
+
+/* Create a solver for N phases (2 <= N <= LBM_MAXN) on the current CUDA device.
+ * Checks the parameters (tau_f, tau_g, tau_h > 1/2 for every phase, sigma symmetric
+ * with zero diagonal, boundary combinations), derives beta_pq, k_pq and c_p,ref on
+ * the host and allocates two population sets of 9 (N + 2) planes and two sets of
+ * 3 + 2N lagged planes.  *out is set to NULL on failure.  The state is undefined
+ * until lbm_set_fields. */
+int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_thermal* thermal,
+               const lbm_bc* bc, const lbm_numerics* numerics, lbm_handle** out);
+
+/* Queue all later work of the handle on `stream` (a cudaStream_t; NULL = default). */
+int lbm_set_stream(lbm_handle* h, void* stream);
+
+/* Initial state at t = 0 from phi [N][ny][nx], T, ux, uy (ux / uy may be NULL = 0):
+ * rho H from the inverse of eq. H (a cell at or above T_liq is liquid), p = 0,
+ * every population at its equilibrium, mdot' = Q' = 0, psi' = psi, (phi u)' = phi u.
+ * Resets the step counter. */
+int lbm_set_fields(lbm_handle* h, const double* phi, const double* T, const double* ux,
+                   const double* uy, int where);
+
+/* Advance nsteps fused time steps (one kernel launch per step on the handle's
+ * stream; asynchronous unless diag_every > 0, which synchronises every K steps and
+ * returns LBM_EUNSTABLE when a non-finite value appears). */
+int lbm_step(lbm_handle* h, long nsteps);
+
+/* Macroscopic fields of the current state (NULL = skip): phi [N][ny][nx], T,
+ * specific enthalpy H = (rho H) / rho, liquid fraction f_l, velocity u and pressure p
+ * (computed from the current populations exactly as the step computes them). */
+int lbm_get_fields(lbm_handle* h, double* phi, double* T, double* H, double* fl, double* ux,
+                   double* uy, double* p, int where);
+
+/* Diagnostics of the current state (synchronises the handle's stream). */
+int lbm_get_diagnostics(lbm_handle* h, lbm_diag* out);
+
+/* Raw state: *bytes receives the size of the checkpoint; buf may be NULL to query.
+ * lbm_save_state copies populations, lagged planes and the step counter to host
+ * memory; lbm_load_state restores them on a handle created with the same grid, N and
+ * precision. */
+int lbm_save_state(lbm_handle* h, void* buf, size_t* bytes);
+int lbm_load_state(lbm_handle* h, const void* buf, size_t bytes);
+
+/* Steps taken since lbm_set_fields / lbm_load_state. */
+long long lbm_get_steps(const lbm_handle* h);
+
+/* Bounds-check record of a library built with -DLBM_CHECK_BOUNDS (every global load
+ * and store of the kernels checks its index against its buffer; a violation is counted
+ * and skipped, never trapped): out3 = {violations, site code of the first, its index}.
+ * Synchronises the handle's stream.  Returns LBM_EINVAL in normal builds. */
+int lbm_debug_bounds(lbm_handle* h, long long* out3);
+
+/* Tile shape (bx, by) of the fused step kernel; 0, 0 restores the default.  The
+ * shape must be one of the compiled variants (LBM_EINVAL otherwise). */
+int lbm_set_tile(lbm_handle* h, int bx, int by);
+
+/* Message of the last failing call on h (or of the last failing lbm_create when
+ * h is NULL).  Never NULL. */
+const char* lbm_last_error(const lbm_handle* h);
+
+void lbm_destroy(lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

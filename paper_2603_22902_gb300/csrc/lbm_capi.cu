@@ -1,0 +1,430 @@
+// lbm_capi.cu -- the C ABI declared in include/lbm.h: handle, parameter checks and
+// derivations (Sections 2-3 of arXiv 2603.22902), device memory, launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_launch.cuh"
+
+using namespace lbm;
+
+struct lbm_handle {
+    int device = 0;
+    int N = 0, nx = 0, ny = 0;
+    int precision = LBM_FP64;
+    int diag_every = 0;
+    int tile = TILE_32x8;
+    KParams P{};
+    double* pop[2] = {nullptr, nullptr};  // 9 (N + 2) planes each
+    double* aux[2] = {nullptr, nullptr};  // 3 + 2N planes each
+    double* io = nullptr;                 // N + 6 planes: staging for host I/O
+    double* diag_partial = nullptr;
+    double* diag_out = nullptr;
+    unsigned long long* dbg = nullptr;    // bounds-check record (LBM_CHECK_BOUNDS builds)
+    int cur = 0;
+    bool ready = false;
+    long long steps = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+};
+
+static thread_local std::string g_create_error;
+
+static int fail(lbm_handle* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+static int cuda_fail(lbm_handle* h, cudaError_t e, const char* where)
+{
+    return fail(h, LBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA_TRY(h, call)                                  \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+// dispatch on the phase count
+#define LBM_DISPATCH_N(N_, CALL) \
+    ((N_) == 2 ? CALL(2) : (N_) == 3 ? CALL(3) : CALL(4))
+
+static size_t plane_bytes(const lbm_handle* h) { return (size_t)h->P.S * sizeof(double); }
+
+static void free_all(lbm_handle* h)
+{
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(h->pop[k]);
+        cudaFree(h->aux[k]);
+        h->pop[k] = h->aux[k] = nullptr;
+    }
+    cudaFree(h->io);
+    cudaFree(h->diag_partial);
+    cudaFree(h->diag_out);
+    cudaFree(h->dbg);
+    h->io = h->diag_partial = h->diag_out = nullptr;
+    h->dbg = nullptr;
+}
+
+extern "C" {
+
+int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_thermal* th, const lbm_bc* bc,
+               const lbm_numerics* num, lbm_handle** out)
+{
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !phases || !th || !bc || !num) return fail(nullptr, LBM_EINVAL, "NULL argument");
+    if (grid->nx < 3 || grid->ny < 3) return fail(nullptr, LBM_EINVAL, "nx and ny must be >= 3");
+    if ((long long)grid->nx * grid->ny > (1LL << 31)) return fail(nullptr, LBM_EINVAL, "grid too large");
+    if (N < 2 || N > LBM_MAXN) return fail(nullptr, LBM_EINVAL, "N must be in [2, 4]");
+    if (num->precision != LBM_FP64)
+        return fail(nullptr, LBM_EINVAL, "precision not available in this build (LBM_FP64 only)");
+    if (!(num->eps > 0.0) || !(num->mobility > 0.0)) return fail(nullptr, LBM_EINVAL, "eps and mobility must be > 0");
+    if (num->diag_every < 0) return fail(nullptr, LBM_EINVAL, "diag_every must be >= 0");
+    if (!(th->T_sol <= th->T_liq)) return fail(nullptr, LBM_EINVAL, "T_sol must be <= T_liq");
+    if (!(th->rho_ref > 0.0) || !(th->cp_ref >= 0.0)) return fail(nullptr, LBM_EINVAL, "rho_ref > 0, cp_ref >= 0");
+    for (int p = 0; p < N; ++p) {
+        const lbm_phase& ph = phases[p];
+        if (!(ph.rho_l > 0.0 && ph.rho_s > 0.0 && ph.cp_l > 0.0 && ph.cp_s > 0.0))
+            return fail(nullptr, LBM_EINVAL, "densities and heat capacities must be > 0");
+        // tau_f = mu / (rho c_s^2) + 1/2 > 1/2 and tau_h = lambda / (rho_ref c_ref c_s^2) + 1/2 > 1/2
+        if (!(ph.mu_l > 0.0 && ph.mu_s > 0.0)) return fail(nullptr, LBM_EINVAL, "viscosities must be > 0 (tau_f > 1/2)");
+        if (!(ph.lambda_l > 0.0 && ph.lambda_s > 0.0))
+            return fail(nullptr, LBM_EINVAL, "conductivities must be > 0 (tau_h > 1/2)");
+        if (!(ph.latent >= 0.0)) return fail(nullptr, LBM_EINVAL, "latent heat must be >= 0");
+        for (int q = 0; q < N; ++q) {
+            const double s = num->sigma[p * LBM_MAXN + q];
+            if (s != num->sigma[q * LBM_MAXN + p] || !(s >= 0.0) || (p == q && s != 0.0))
+                return fail(nullptr, LBM_EINVAL, "sigma must be symmetric, >= 0, zero on the diagonal");
+        }
+    }
+    for (int s = 0; s < 4; ++s) {
+        if (bc->kind[s] < LBM_BC_PERIODIC || bc->kind[s] > LBM_BC_OUTFLOW) return fail(nullptr, LBM_EINVAL, "bad bc kind");
+        if (bc->tkind[s] != LBM_T_ADIABATIC && bc->tkind[s] != LBM_T_DIRICHLET)
+            return fail(nullptr, LBM_EINVAL, "bad thermal bc kind");
+        if (s < 2 && bc->kind[s] == LBM_BC_OUTFLOW) return fail(nullptr, LBM_EINVAL, "outflow only on y sides");
+        if (bc->tkind[s] == LBM_T_DIRICHLET && (s < 2 || bc->kind[s] != LBM_BC_WALL))
+            return fail(nullptr, LBM_EINVAL, "Dirichlet temperature only on y-side walls");
+    }
+    if ((bc->kind[0] == LBM_BC_PERIODIC) != (bc->kind[1] == LBM_BC_PERIODIC) ||
+        (bc->kind[2] == LBM_BC_PERIODIC) != (bc->kind[3] == LBM_BC_PERIODIC))
+        return fail(nullptr, LBM_EINVAL, "periodic sides must come in pairs");
+
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(nullptr, LBM_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    h->N = N;
+    h->nx = grid->nx;
+    h->ny = grid->ny;
+    h->precision = num->precision;
+    h->diag_every = num->diag_every;
+
+    KParams& P = h->P;
+    P.nx = grid->nx;
+    P.ny = grid->ny;
+    P.N = N;
+    P.S = (long long)grid->nx * grid->ny;
+    for (int s = 0; s < 4; ++s) {
+        P.bc[s] = bc->kind[s];
+        P.tbc[s] = bc->tkind[s];
+        P.Tw[s] = bc->T_wall[s];
+    }
+    for (int p = 0; p < N; ++p) {
+        const lbm_phase& ph = phases[p];
+        P.rho_l[p] = ph.rho_l;
+        P.rho_s[p] = ph.rho_s;
+        P.mu_l[p] = ph.mu_l;
+        P.mu_s[p] = ph.mu_s;
+        P.lam_l[p] = ph.lambda_l;
+        P.lam_s[p] = ph.lambda_s;
+        P.cp_l[p] = ph.cp_l;
+        P.cp_s[p] = ph.cp_s;
+        P.rhoL[p] = ph.rho_l * ph.latent;
+        P.drho[p] = ph.rho_s - ph.rho_l;
+        P.pcm[p] = ph.latent > 0.0 ? 1.0 : 0.0;
+        for (int q = 0; q < N; ++q) {
+            const double sig = num->sigma[p * LBM_MAXN + q];
+            P.b2[p][q] = 2.0 * 3.0 / num->eps * sig;      // 2 beta_pq
+            P.kk[p][q] = 3.0 * num->eps / 4.0 * sig;      // -k_pq
+            for (int s = 0; s < 4; ++s)
+                P.wet[s][p][q] = bc->kind[s] == LBM_BC_WALL ? 4.0 / num->eps * bc->wet_cos[s][p * LBM_MAXN + q] : 0.0;
+        }
+    }
+    P.four_eps = 4.0 / num->eps;
+    P.T_sol = th->T_sol;
+    P.T_liq = th->T_liq;
+    const double cp_ref = th->cp_ref > 0.0 ? th->cp_ref
+                                           : 2.0 * phases[0].cp_s * phases[0].cp_l / (phases[0].cp_s + phases[0].cp_l);
+    P.E_ref = th->rho_ref * cp_ref;
+    P.tau_h_scale = 3.0 / P.E_ref;
+    P.us[0] = th->u_solid[0];
+    P.us[1] = th->u_solid[1];
+    P.accel[0] = th->accel[0];
+    P.accel[1] = th->accel[1];
+    const double tau_g = num->mobility * 3.0 + 0.5;
+    P.omega_g = 1.0 / tau_g;
+    P.kg = 1.0 - 0.5 * P.omega_g;
+
+    const size_t pb = plane_bytes(h);
+    const size_t npop = npop_planes(N), naux = naux_planes(N);
+    P.pop_elems = (long long)npop * P.S;
+    P.aux_elems = (long long)naux * P.S;
+    P.dbg = nullptr;
+    const int nb = diag_blocks(P.S);
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok = cudaMalloc(&h->pop[k], npop * pb) == cudaSuccess && cudaMalloc(&h->aux[k], naux * pb) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&h->io, (size_t)(N + 6) * pb) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->diag_partial, (size_t)nb * (2 * N + 2) * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->diag_out, (size_t)(2 * N + 2) * sizeof(double)) == cudaSuccess;
+#ifdef LBM_CHECK_BOUNDS
+    ok = ok && cudaMalloc(&h->dbg, 3 * sizeof(unsigned long long)) == cudaSuccess &&
+         cudaMemset(h->dbg, 0, 3 * sizeof(unsigned long long)) == cudaSuccess;
+    P.dbg = h->dbg;
+#endif
+    if (!ok) {
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return fail(nullptr, LBM_ENOMEM, "device allocation failed");
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_handle* h, void* stream)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    h->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+int lbm_set_tile(lbm_handle* h, int bx, int by)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (bx == 0 && by == 0) {
+        h->tile = TILE_32x8;
+        return LBM_OK;
+    }
+    for (int id = 0; id < TILE_COUNT; ++id) {
+        int tx, ty;
+        tile_dims(id, tx, ty);
+        if (tx == bx && ty == by) {
+            h->tile = id;
+            return LBM_OK;
+        }
+    }
+    return fail(h, LBM_EINVAL, "tile shape not compiled (32x8, 32x4, 64x4, 16x16)");
+}
+
+int lbm_set_fields(lbm_handle* h, const double* phi, const double* T, const double* ux, const double* uy, int where)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!phi || !T) return fail(h, LBM_EINVAL, "phi and T are required");
+    if (where != LBM_HOST && where != LBM_DEVICE) return fail(h, LBM_EINVAL, "bad where");
+    LBM_CUDA_TRY(h, cudaSetDevice(h->device));
+    const size_t pb = plane_bytes(h);
+    const double *dphi = phi, *dT = T, *dux = ux, *duy = uy;
+    if (where == LBM_HOST) {
+        double* s = h->io;
+        LBM_CUDA_TRY(h, cudaMemcpyAsync(s, phi, h->N * pb, cudaMemcpyHostToDevice, h->stream));
+        LBM_CUDA_TRY(h, cudaMemcpyAsync(s + h->N * h->P.S, T, pb, cudaMemcpyHostToDevice, h->stream));
+        dphi = s;
+        dT = s + h->N * h->P.S;
+        if (ux) {
+            LBM_CUDA_TRY(h, cudaMemcpyAsync(s + (h->N + 1) * h->P.S, ux, pb, cudaMemcpyHostToDevice, h->stream));
+            dux = s + (h->N + 1) * h->P.S;
+        }
+        if (uy) {
+            LBM_CUDA_TRY(h, cudaMemcpyAsync(s + (h->N + 2) * h->P.S, uy, pb, cudaMemcpyHostToDevice, h->stream));
+            duy = s + (h->N + 2) * h->P.S;
+        }
+    }
+    h->cur = 0;
+#define LBM_CALL_INIT(NN) launch_init<NN>(h->P, dphi, dT, dux, duy, h->pop[0], h->aux[0], h->stream)
+    cudaError_t e = LBM_DISPATCH_N(h->N, LBM_CALL_INIT);
+#undef LBM_CALL_INIT
+    if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+    if (where == LBM_HOST) LBM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->ready = true;
+    h->steps = 0;
+    return LBM_OK;
+}
+
+static int run_diag(lbm_handle* h, double* host_out)
+{
+#define LBM_CALL_DIAG(NN) launch_diag<NN>(h->P, h->pop[h->cur], h->aux[h->cur], h->diag_partial, h->diag_out, h->stream)
+    cudaError_t e = LBM_DISPATCH_N(h->N, LBM_CALL_DIAG);
+#undef LBM_CALL_DIAG
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics kernel");
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(host_out, h->diag_out, (2 * h->N + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream));
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle* h, long nsteps)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!h->ready) return fail(h, LBM_ESTATE, "lbm_set_fields has not been called");
+    if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
+    LBM_CUDA_TRY(h, cudaSetDevice(h->device));
+    for (long n = 0; n < nsteps; ++n) {
+        const int a = h->cur, b = a ^ 1;
+#define LBM_CALL_STEP(NN) launch_step<NN>(h->P, h->pop[a], h->pop[b], h->aux[a], h->aux[b], h->tile, h->stream)
+        cudaError_t e = LBM_DISPATCH_N(h->N, LBM_CALL_STEP);
+#undef LBM_CALL_STEP
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+        h->cur = b;
+        h->steps++;
+        if (h->diag_every > 0 && h->steps % h->diag_every == 0) {
+            double d[2 * LBM_MAXN + 2];
+            int rc = run_diag(h, d);
+            if (rc != LBM_OK) return rc;
+            if (d[2 * h->N + 1] > 0.0) return fail(h, LBM_EUNSTABLE, "non-finite value in the state");
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_get_fields(lbm_handle* h, double* phi, double* T, double* H, double* fl, double* ux, double* uy, double* p,
+                   int where)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!h->ready) return fail(h, LBM_ESTATE, "lbm_set_fields has not been called");
+    if (where != LBM_HOST && where != LBM_DEVICE) return fail(h, LBM_EINVAL, "bad where");
+    LBM_CUDA_TRY(h, cudaSetDevice(h->device));
+    const long long S = h->P.S;
+    double* user[7] = {phi, T, H, fl, ux, uy, p};
+    double* dev[7];
+    if (where == LBM_DEVICE) {
+        for (int k = 0; k < 7; ++k) dev[k] = user[k];
+    } else {
+        long long off = 0;
+        for (int k = 0; k < 7; ++k) {
+            dev[k] = user[k] ? h->io + off : nullptr;
+            off += (k == 0 ? h->N : 1) * S;
+        }
+    }
+#define LBM_CALL_EXPORT(NN) \
+    launch_export<NN>(h->P, h->pop[h->cur], h->aux[h->cur], dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dev[6], h->stream)
+    cudaError_t e = LBM_DISPATCH_N(h->N, LBM_CALL_EXPORT);
+#undef LBM_CALL_EXPORT
+    if (e != cudaSuccess) return cuda_fail(h, e, "export kernel");
+    if (where == LBM_HOST) {
+        for (int k = 0; k < 7; ++k)
+            if (user[k])
+                LBM_CUDA_TRY(h, cudaMemcpyAsync(user[k], dev[k], (k == 0 ? h->N : 1) * plane_bytes(h),
+                                                cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    }
+    return LBM_OK;
+}
+
+int lbm_get_diagnostics(lbm_handle* h, lbm_diag* out)
+{
+    if (!h || !out) return fail(h, LBM_EINVAL, "NULL argument");
+    if (!h->ready) return fail(h, LBM_ESTATE, "lbm_set_fields has not been called");
+    LBM_CUDA_TRY(h, cudaSetDevice(h->device));
+    double d[2 * LBM_MAXN + 2];
+    int rc = run_diag(h, d);
+    if (rc != LBM_OK) return rc;
+    std::memset(out, 0, sizeof *out);
+    for (int p = 0; p < h->N; ++p) {
+        out->mass[p] = d[p];
+        out->solid[p] = d[h->N + p];
+    }
+    out->max_sum_dev = d[2 * h->N];
+    out->nonfinite = (long long)d[2 * h->N + 1];
+    out->steps = h->steps;
+    return LBM_OK;
+}
+
+int lbm_save_state(lbm_handle* h, void* buf, size_t* bytes)
+{
+    if (!h || !bytes) return fail(h, LBM_EINVAL, "NULL argument");
+    const size_t pb = plane_bytes(h);
+    const size_t need = sizeof(long long) + (npop_planes(h->N) + naux_planes(h->N)) * pb;
+    if (!buf) {
+        *bytes = need;
+        return LBM_OK;
+    }
+    if (!h->ready) return fail(h, LBM_ESTATE, "lbm_set_fields has not been called");
+    if (*bytes < need) return fail(h, LBM_EINVAL, "buffer too small");
+    LBM_CUDA_TRY(h, cudaSetDevice(h->device));
+    char* b = (char*)buf;
+    std::memcpy(b, &h->steps, sizeof(long long));
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(b + sizeof(long long), h->pop[h->cur], npop_planes(h->N) * pb,
+                                    cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(b + sizeof(long long) + npop_planes(h->N) * pb, h->aux[h->cur],
+                                    naux_planes(h->N) * pb, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    *bytes = need;
+    return LBM_OK;
+}
+
+int lbm_load_state(lbm_handle* h, const void* buf, size_t bytes)
+{
+    if (!h || !buf) return fail(h, LBM_EINVAL, "NULL argument");
+    const size_t pb = plane_bytes(h);
+    const size_t need = sizeof(long long) + (npop_planes(h->N) + naux_planes(h->N)) * pb;
+    if (bytes != need) return fail(h, LBM_EINVAL, "state size does not match this handle");
+    LBM_CUDA_TRY(h, cudaSetDevice(h->device));
+    const char* b = (const char*)buf;
+    long long steps;
+    std::memcpy(&steps, b, sizeof(long long));
+    h->cur = 0;
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(h->pop[0], b + sizeof(long long), npop_planes(h->N) * pb, cudaMemcpyHostToDevice,
+                                    h->stream));
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(h->aux[0], b + sizeof(long long) + npop_planes(h->N) * pb,
+                                    naux_planes(h->N) * pb, cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->steps = steps;
+    h->ready = true;
+    return LBM_OK;
+}
+
+long long lbm_get_steps(const lbm_handle* h) { return h ? h->steps : -1; }
+
+int lbm_debug_bounds(lbm_handle* h, long long* out3)
+{
+    if (!h || !out3) return fail(h, LBM_EINVAL, "NULL argument");
+#ifdef LBM_CHECK_BOUNDS
+    unsigned long long v[3];
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    LBM_CUDA_TRY(h, cudaMemcpy(v, h->dbg, sizeof v, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 3; ++k) out3[k] = (long long)v[k];
+    return LBM_OK;
+#else
+    return fail(h, LBM_EINVAL, "library built without LBM_CHECK_BOUNDS");
+#endif
+}
+
+const char* lbm_last_error(const lbm_handle* h)
+{
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+void lbm_destroy(lbm_handle* h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

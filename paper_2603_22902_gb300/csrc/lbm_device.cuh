@@ -1,0 +1,147 @@
+// lbm_device.cuh -- device-side constants, parameter block and cell-local
+// physics of the coupled LB step (arXiv 2603.22902, Sections 2-3).
+#pragma once
+
+#include <cstdint>
+
+namespace lbm {
+
+constexpr int MAXN = 4;
+constexpr int PERIODIC = 0, WALL = 1, OUTFLOW = 2;
+constexpr int ADIABATIC = 0, DIRICHLET = 1;
+
+// D2Q9: c_0 = 0; c_1..4 = (1,0), (0,1), (-1,0), (0,-1); c_5..8 the diagonals.
+__host__ __device__ constexpr int cx(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }
+__host__ __device__ constexpr int cy(int i) { return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0); }
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i < 5 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5); }
+__host__ __device__ constexpr double wgt(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+// Parameter block passed by value to every kernel (lives in the constant bank).
+// Everything derivable once per run is derived on the host.
+struct KParams {
+    int nx, ny, N;
+    long long S;                  // plane stride in elements (nx * ny)
+    int bc[4], tbc[4];            // side kinds, sides 0 x-min, 1 x-max, 2 y-min, 3 y-max
+    double Tw[4];                 // Dirichlet wall temperature
+    // eq. 2 mixture coefficients per phase
+    double rho_l[MAXN], rho_s[MAXN], mu_l[MAXN], mu_s[MAXN];
+    double lam_l[MAXN], lam_s[MAXN], cp_l[MAXN], cp_s[MAXN];
+    double rhoL[MAXN];            // rho_l^p L_p: latent heat per volume of pure phase p
+    double drho[MAXN];            // rho_s^p - rho_l^p
+    double pcm[MAXN];             // 1 where L_p > 0 (the phase changes phase), else 0
+    // Section 2 free energy: 2 beta_pq = 6 sigma_pq / eps and -k_pq = 3 eps sigma_pq / 4
+    double b2[MAXN][MAXN], kk[MAXN][MAXN];
+    double four_eps;              // 4 / eps
+    double wet[4][MAXN][MAXN];    // (4 / eps) cos(theta_pq) per wall side (0 elsewhere)
+    double T_sol, T_liq;
+    double E_ref;                 // rho_ref c_p,ref
+    double tau_h_scale;           // 1 / (rho_ref c_p,ref c_s^2)
+    double us[2], accel[2];
+    double omega_g, kg;           // 1 / tau_g and 1 - 1/(2 tau_g), tau_g = M / c_s^2 + 1/2
+    long long pop_elems, aux_elems;  // sizes of one population set / one lagged set (elements)
+    unsigned long long* dbg;      // LBM_CHECK_BOUNDS builds: {violations, first site, first index}
+};
+
+// Global-memory access with an optional bounds check.  In LBM_CHECK_BOUNDS builds an
+// out-of-range index is recorded in P.dbg (count, site code, index) and the access is
+// skipped (a load returns 0); nothing traps.  Normal builds compile to the plain access.
+#ifdef LBM_CHECK_BOUNDS
+__device__ __forceinline__ bool lbm_in_bounds(unsigned long long* dbg, long long idx, long long lim, int site)
+{
+    if (idx >= 0 && idx < lim) return true;
+    if (dbg && atomicAdd(dbg, 1ull) == 0ull) {
+        dbg[1] = (unsigned long long)site;
+        dbg[2] = (unsigned long long)idx;
+    }
+    return false;
+}
+#define LBM_LD(P_, ptr, idx, lim, site) (lbm_in_bounds((P_).dbg, (idx), (lim), (site)) ? __ldg((ptr) + (idx)) : 0.0)
+#define LBM_ST(P_, ptr, idx, lim, site, val)                                  \
+    do {                                                                      \
+        if (lbm_in_bounds((P_).dbg, (idx), (lim), (site))) (ptr)[idx] = (val); \
+    } while (0)
+#else
+#define LBM_LD(P_, ptr, idx, lim, site) __ldg((ptr) + (idx))
+#define LBM_ST(P_, ptr, idx, lim, site, val) ((ptr)[idx] = (val))
+#endif
+
+// Plane layout of one population set: f[0..8], g_0[0..8] .. g_{N-1}[0..8], h[0..8].
+__host__ __device__ constexpr int plane_f(int i) { return i; }
+__host__ __device__ constexpr int plane_g(int p, int i) { return 9 + 9 * p + i; }
+__host__ __device__ constexpr int plane_h(int N, int i) { return 9 + 9 * N + i; }
+__host__ __device__ constexpr int npop_planes(int N) { return 9 * (N + 2); }
+// Lagged planes: mdot', Q', psi', (phi_p u)' x N, (phi_p u)' y N.
+__host__ __device__ constexpr int aux_mdot() { return 0; }
+__host__ __device__ constexpr int aux_Q() { return 1; }
+__host__ __device__ constexpr int aux_psi() { return 2; }
+__host__ __device__ constexpr int aux_phiux(int p) { return 3 + p; }
+__host__ __device__ constexpr int aux_phiuy(int N, int p) { return 3 + N + p; }
+__host__ __device__ constexpr int naux_planes(int N) { return 3 + 2 * N; }
+
+// Mixture (eq. 2) sums over the phases.
+template <int N>
+struct Mix {
+    double rs, rl, cs, cl, Lv, dr, pcm;
+};
+
+template <int N>
+__device__ __forceinline__ Mix<N> mixture_core(const KParams& P, const double (&phi)[N])
+{
+    Mix<N> m{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        m.rs = fma(phi[p], P.rho_s[p], m.rs);
+        m.rl = fma(phi[p], P.rho_l[p], m.rl);
+        m.cs = fma(phi[p], P.cp_s[p], m.cs);
+        m.cl = fma(phi[p], P.cp_l[p], m.cl);
+        m.Lv = fma(phi[p], P.rhoL[p], m.Lv);
+        m.dr = fma(phi[p], P.drho[p], m.dr);
+        m.pcm = fma(phi[p], P.pcm[p], m.pcm);
+    }
+    return m;
+}
+
+// eq. H: liquid fraction (and, with WANT_T, temperature) from rho H.
+// rho_s H_s = rs cs T_sol, rho_l H_l = rl cl T_liq + Lv; a cell without phase-changing
+// material (Lv <= 0) is liquid (the ambient fluid has f_s = 0).
+template <int N, bool WANT_T>
+__device__ __forceinline__ void enthalpy_map(const KParams& P, const Mix<N>& m, double rhoH, double& fl, double& T)
+{
+    const double rcs = m.rs * m.cs, rcl = m.rl * m.cl;
+    const double As = rcs * P.T_sol;
+    const double Al = fma(rcl, P.T_liq, m.Lv);
+    if (!(m.Lv > 0.0)) {
+        fl = 1.0;
+        if (WANT_T) T = P.T_liq + (rhoH - Al) / rcl;
+    } else if (rhoH < As) {
+        fl = 0.0;
+        if (WANT_T) T = rhoH / rcs;
+    } else if (rhoH > Al) {
+        fl = 1.0;
+        if (WANT_T) T = P.T_liq + (rhoH - Al) / rcl;
+    } else if (Al - As > 0.0) {
+        fl = (rhoH - As) / (Al - As);
+        if (WANT_T) T = fma(fl, P.T_liq - P.T_sol, P.T_sol);
+    } else {
+        fl = 1.0;
+        if (WANT_T) T = P.T_liq;
+    }
+}
+
+// Inverse of eq. H at t = 0 (a cell at or above the liquidus is liquid).
+template <int N>
+__device__ __forceinline__ double inverse_map(const KParams& P, const Mix<N>& m, double T)
+{
+    const double rcs = m.rs * m.cs, rcl = m.rl * m.cl;
+    const double As = rcs * P.T_sol;
+    const double Al = fma(rcl, P.T_liq, m.Lv);
+    if (!(m.Lv > 0.0)) return Al + rcl * (T - P.T_liq);
+    if (T < P.T_sol) return rcs * T;
+    if (T >= P.T_liq) return Al + rcl * (T - P.T_liq);
+    return As + (T - P.T_sol) / (P.T_liq - P.T_sol) * (Al - As);
+}
+
+// g'(x) for g(x) = x^2 (1 - x)^2
+__device__ __forceinline__ double gprime(double x) { return 2.0 * x * (1.0 - x) * (1.0 - 2.0 * x); }
+
+}  // namespace lbm

@@ -1,0 +1,48 @@
+// lbm_launch.cuh -- host-side launchers of the device kernels, one explicit
+// instantiation set per phase count N (lbm_kernels_n{2,3,4}.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+struct ExportPtrs;
+
+// Compiled tile shapes of the fused step kernel (TX x TY threads, one cell each).
+enum TileId { TILE_32x8 = 0, TILE_32x4 = 1, TILE_64x4 = 2, TILE_16x16 = 3, TILE_COUNT = 4 };
+inline bool tile_dims(int id, int& tx, int& ty)
+{
+    switch (id) {
+        case TILE_32x8: tx = 32; ty = 8; return true;
+        case TILE_32x4: tx = 32; ty = 4; return true;
+        case TILE_64x4: tx = 64; ty = 4; return true;
+        case TILE_16x16: tx = 16; ty = 16; return true;
+        default: return false;
+    }
+}
+
+template <int N>
+cudaError_t launch_step(const KParams& P, const double* pin, double* pout, const double* ain, double* aout,
+                        int tile, cudaStream_t st);
+template <int N>
+cudaError_t launch_export(const KParams& P, const double* pin, const double* ain, double* phi, double* T,
+                          double* H, double* fl, double* ux, double* uy, double* p, cudaStream_t st);
+template <int N>
+cudaError_t launch_init(const KParams& P, const double* phi, const double* T, const double* ux, const double* uy,
+                        double* pop, double* aux, cudaStream_t st);
+// Two-pass deterministic reduction; partial must hold diag_blocks() * (2N + 2) doubles,
+// out 2N + 2 doubles (mass[N], solid[N], max |sum phi - 1|, non-finite count).
+constexpr int DIAG_NT = 256;
+inline int diag_blocks(long long cells)
+{
+    long long b = (cells + DIAG_NT - 1) / DIAG_NT;
+    if (b > 4 * 152) b = 4 * 152;  // a few blocks per SM of a GB300 is enough
+    return (int)(b < 1 ? 1 : b);
+}
+template <int N>
+cudaError_t launch_diag(const KParams& P, const double* pop, const double* aux, double* partial, double* out,
+                        cudaStream_t st);
+
+}  // namespace lbm

@@ -1,0 +1,289 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h`` (argument marshalling only).
+
+Every step of the solver runs in ``liblbm_gb300.so`` (sm_103a CUDA kernels).  There
+is no Python or CPU fallback: if the library is missing or no CUDA device is present
+the calls raise.  PyTorch is used only for device buffers and the current stream.
+
+The module exposes the C functions under their C names (``lbm_create``,
+``lbm_set_fields``, ``lbm_step``, ``lbm_get_fields`` ...) plus ``Solver``, a small
+owner object that builds the parameter structures from a ``workloads.Case``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm_gb300.so")
+# LBM_CHECK_BOUNDS=1 selects the bounds-checked debug build (liblbm_gb300_check.so)
+if os.environ.get("LBM_CHECK_BOUNDS") == "1":
+    LIB_PATH = os.path.join(HERE, "liblbm_gb300_check.so")
+
+MAXN = 4
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
+LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_OUTFLOW = 0, 1, 2
+LBM_T_ADIABATIC, LBM_T_DIRICHLET = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S = 0, 1, 2, 3
+LBM_HOST, LBM_DEVICE = 0, 1
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
+
+_D = ctypes.c_double
+
+
+class lbm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int)]
+
+
+class lbm_phase(ctypes.Structure):
+    _fields_ = [(n, _D) for n in ("rho_l", "rho_s", "mu_l", "mu_s", "lambda_l", "lambda_s", "cp_l", "cp_s", "latent")]
+
+
+class lbm_thermal(ctypes.Structure):
+    _fields_ = [("T_sol", _D), ("T_liq", _D), ("rho_ref", _D), ("cp_ref", _D),
+                ("u_solid", _D * 2), ("accel", _D * 2)]
+
+
+class lbm_bc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int * 4), ("tkind", ctypes.c_int * 4), ("T_wall", _D * 4),
+                ("wet_cos", (_D * (MAXN * MAXN)) * 4)]
+
+
+class lbm_numerics(ctypes.Structure):
+    _fields_ = [("eps", _D), ("mobility", _D), ("sigma", _D * (MAXN * MAXN)),
+                ("precision", ctypes.c_int), ("diag_every", ctypes.c_int)]
+
+
+class lbm_diag(ctypes.Structure):
+    _fields_ = [("mass", _D * MAXN), ("solid", _D * MAXN), ("max_sum_dev", _D),
+                ("nonfinite", ctypes.c_longlong), ("steps", ctypes.c_longlong)]
+
+
+_lib = None
+_lock = threading.Lock()
+_VP = ctypes.c_void_p
+
+
+def library():
+    """Load liblbm_gb300.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with paper_2603_22902_gb300.build.build() "
+                    "(nvcc, sm_103a); there is no CPU fallback")
+            lib = ctypes.CDLL(LIB_PATH)
+            P = ctypes.POINTER
+            lib.lbm_create.argtypes = [P(lbm_grid), ctypes.c_int, P(lbm_phase), P(lbm_thermal), P(lbm_bc),
+                                       P(lbm_numerics), P(_VP)]
+            lib.lbm_set_stream.argtypes = [_VP, _VP]
+            lib.lbm_set_fields.argtypes = [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]
+            lib.lbm_step.argtypes = [_VP, ctypes.c_long]
+            lib.lbm_get_fields.argtypes = [_VP] + [_VP] * 7 + [ctypes.c_int]
+            lib.lbm_get_diagnostics.argtypes = [_VP, P(lbm_diag)]
+            lib.lbm_save_state.argtypes = [_VP, _VP, P(ctypes.c_size_t)]
+            lib.lbm_load_state.argtypes = [_VP, _VP, ctypes.c_size_t]
+            lib.lbm_get_steps.argtypes = [_VP]
+            lib.lbm_get_steps.restype = ctypes.c_longlong
+            lib.lbm_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+            lib.lbm_debug_bounds.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong)]
+            lib.lbm_debug_bounds.restype = ctypes.c_int
+            lib.lbm_last_error.argtypes = [_VP]
+            lib.lbm_last_error.restype = ctypes.c_char_p
+            lib.lbm_destroy.argtypes = [_VP]
+            for name in ("lbm_create", "lbm_set_stream", "lbm_set_fields", "lbm_step", "lbm_get_fields",
+                         "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile"):
+                getattr(lib, name).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def _check(rc, h=None):
+    if rc != LBM_OK:
+        msg = library().lbm_last_error(h).decode(errors="replace")
+        raise LBMError(rc, msg)
+    return rc
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor, host pointer of a numpy array, or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+# ---- C functions under their C names --------------------------------------
+
+def lbm_create(grid, N, phases, thermal, bc, numerics):
+    h = _VP()
+    arr = (lbm_phase * N)(*phases)
+    _check(library().lbm_create(ctypes.byref(grid), N, arr, ctypes.byref(thermal), ctypes.byref(bc),
+                                ctypes.byref(numerics), ctypes.byref(h)))
+    return h
+
+
+def lbm_set_stream(h, stream_ptr):
+    return _check(library().lbm_set_stream(h, stream_ptr), h)
+
+
+def lbm_set_fields(h, phi, T, ux, uy, where):
+    return _check(library().lbm_set_fields(h, _ptr(phi), _ptr(T), _ptr(ux), _ptr(uy), where), h)
+
+
+def lbm_step(h, nsteps):
+    return _check(library().lbm_step(h, int(nsteps)), h)
+
+
+def lbm_get_fields(h, phi, T, H, fl, ux, uy, p, where):
+    return _check(library().lbm_get_fields(h, *[_ptr(a) for a in (phi, T, H, fl, ux, uy, p)], where), h)
+
+
+def lbm_get_diagnostics(h, N):
+    d = lbm_diag()
+    _check(library().lbm_get_diagnostics(h, ctypes.byref(d)), h)
+    return dict(mass=list(d.mass[:N]), solid=list(d.solid[:N]), max_sum_dev=d.max_sum_dev,
+                nonfinite=int(d.nonfinite), steps=int(d.steps))
+
+
+def lbm_save_state(h) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(library().lbm_save_state(h, None, ctypes.byref(n)), h)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(library().lbm_save_state(h, buf, ctypes.byref(n)), h)
+    return buf.raw
+
+
+def lbm_load_state(h, data: bytes):
+    buf = ctypes.create_string_buffer(data, len(data))
+    return _check(library().lbm_load_state(h, buf, len(data)), h)
+
+
+def lbm_get_steps(h) -> int:
+    return int(library().lbm_get_steps(h))
+
+
+def lbm_set_tile(h, bx, by):
+    return _check(library().lbm_set_tile(h, bx, by), h)
+
+
+def lbm_debug_bounds(h):
+    out = (ctypes.c_longlong * 3)()
+    _check(library().lbm_debug_bounds(h, out), h)
+    return list(out)
+
+
+def lbm_destroy(h):
+    library().lbm_destroy(h)
+
+
+# ---- parameter structures from a case ---------------------------------------
+
+def make_structs(case, precision="fp64", diag_every=0):
+    grid = lbm_grid(case.nx, case.ny)
+    phases = [lbm_phase(ph["rho_l"], ph["rho_s"], ph["mu_l"], ph["mu_s"], ph["lam_l"], ph["lam_s"],
+                        ph["cp_l"], ph["cp_s"], ph["latent"]) for ph in case.phases]
+    th = lbm_thermal()
+    th.T_sol, th.T_liq, th.rho_ref, th.cp_ref = case.T_sol, case.T_liq, case.rho_ref, case.cp_ref
+    th.u_solid[0], th.u_solid[1] = case.u_solid
+    th.accel[0], th.accel[1] = case.accel
+    bc = lbm_bc()
+    wc = np.asarray(case.wet_cos, dtype=np.float64).reshape(4, case.N, case.N)
+    for s in range(4):
+        bc.kind[s], bc.tkind[s], bc.T_wall[s] = case.bc[s], case.tbc[s], case.T_wall[s]
+        for p in range(case.N):
+            for q in range(case.N):
+                bc.wet_cos[s][p * MAXN + q] = wc[s, p, q]
+    num = lbm_numerics()
+    num.eps, num.mobility = case.eps, case.mobility
+    sig = np.asarray(case.sigma, dtype=np.float64)
+    for p in range(case.N):
+        for q in range(case.N):
+            num.sigma[p * MAXN + q] = sig[p, q]
+    num.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    num.diag_every = diag_every
+    return grid, phases, th, bc, num
+
+
+class Solver:
+    """One solver handle on the current CUDA device, fed from a ``workloads.Case``."""
+
+    def __init__(self, case, precision="fp64", diag_every=0, tile=None, stream=None):
+        import torch
+        self.torch = torch
+        self.case = case
+        self.N, self.nx, self.ny = case.N, case.nx, case.ny
+        grid, phases, th, bc, num = make_structs(case, precision, diag_every)
+        self.h = lbm_create(grid, case.N, phases, th, bc, num)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        lbm_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream))
+        if tile is not None:
+            lbm_set_tile(self.h, *tile)
+
+    def set_fields(self, phi=None, T=None, ux=None, uy=None):
+        """Initial state from device tensors (default: the case's own fields)."""
+        t = self.torch
+        dev = t.device("cuda")
+        c = self.case
+        conv = lambda a: a.to(dev, t.float64).contiguous() if isinstance(a, t.Tensor) else \
+            t.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+        self._init = [conv(c.phi if phi is None else phi), conv(c.T if T is None else T),
+                      conv(c.ux if ux is None else ux), conv(c.uy if uy is None else uy)]
+        lbm_set_fields(self.h, *self._init, LBM_DEVICE)
+        return self
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+        return self
+
+    @property
+    def steps(self):
+        return lbm_get_steps(self.h)
+
+    def fields(self):
+        """phi[N,ny,nx], T, H, fl, ux, uy, p as float64 device tensors (stream-ordered)."""
+        t = self.torch
+        ny, nx = self.ny, self.nx
+        out = {k: t.empty((ny, nx), dtype=t.float64, device="cuda") for k in ("T", "H", "fl", "ux", "uy", "p")}
+        out["phi"] = t.empty((self.N, ny, nx), dtype=t.float64, device="cuda")
+        lbm_get_fields(self.h, out["phi"], out["T"], out["H"], out["fl"], out["ux"], out["uy"], out["p"], LBM_DEVICE)
+        return out
+
+    def fields_numpy(self):
+        F = self.fields()
+        self.torch.cuda.current_stream().synchronize()
+        return {k: v.cpu().numpy() for k, v in F.items()}
+
+    def diagnostics(self):
+        return lbm_get_diagnostics(self.h, self.N)
+
+    def save_state(self) -> bytes:
+        return lbm_save_state(self.h)
+
+    def load_state(self, data: bytes):
+        lbm_load_state(self.h, data)
+        return self
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

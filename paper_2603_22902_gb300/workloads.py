@@ -199,7 +199,7 @@ def compound_drop(n=1024, R_core=80.0, R_shell=160.0, ste=0.2, seed=3, noise=1e-
         phi1 = np.clip(phi1 + xi[0], 0.0, 1.0)
         phi2 = np.clip(phi2 + xi[1], 0.0, 1.0)
         over = phi1 + phi2
-        scale = np.where(over > 1.0, 1.0 / over, 1.0)
+        scale = 1.0 / np.maximum(over, 1.0)
         phi1, phi2 = phi1 * scale, phi2 * scale
     phi3 = 1.0 - phi1 - phi2
     phi = np.stack([phi1, phi2, np.maximum(phi3, 0.0)])
