@@ -31,10 +31,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "coupled-step MLUPS and % HBM roofline at 1 GB300; reduced-precision vs FP64 at stated error"
 # Algorithmic bytes per lattice update of the fused step: every population read and
-# written once, every lagged plane read and written once, 8 bytes each (FP64):
-# 2 * 8 * (9 (N + 2) + 3 + 2 N).
-def bytes_per_lu(N: int, elem: int = 8) -> int:
-    return 2 * elem * (9 * (N + 2) + 3 + 2 * N)
+# written once, every lagged plane read and written once:
+# 2 [ (N + 2) rest + 8 (N + 2) moving populations + (3 + 2 N) lagged planes ],
+# with (rest, moving, lagged) element sizes of (8, 8, 8) for FP64 (688 B at N = 2),
+# (4, 4, 4) for FP32 and (4, 2, 4) for the 16-bit storage policies.
+ELEM = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "fp16s": (4, 2, 4), "bf16s": (4, 2, 4)}
+
+
+def bytes_per_lu(N: int, precision: str = "fp64") -> int:
+    er, em, ea = ELEM[precision]
+    return 2 * ((N + 2) * er + 8 * (N + 2) * em + (3 + 2 * N) * ea)
 
 
 # FP64 operations per lattice update of the fused step kernel (collision path), counted
@@ -231,13 +237,13 @@ def run_gpu(args):
     value = world * cells * args.steps / (t_ms_max * 1e-3) / 1e6          # MLUPS, all ranks
     mlups_rank = cells * args.steps / (t_ms * 1e-3) / 1e6
     hbm_peak, peak_kind = load_peaks()
-    bpl = bytes_per_lu(N)
+    bpl = bytes_per_lu(N, args.precision)
     gbs = bpl * mlups_rank * 1e6 / 1e9
     roof_hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(gbs / hbm_peak, 4), "traffic": args.traffic,
                 "peak_kind": peak_kind, "bytes_per_lu": bpl}
     roofline = roof_hbm
-    flop = FP64_FLOP_PER_LU.get(N)
+    flop = FP64_FLOP_PER_LU.get(N) if args.precision == "fp64" else None
     alu = None
     if flop:
         tf = flop * mlups_rank * 1e6 / 1e12

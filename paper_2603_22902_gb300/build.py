@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
 LIB_CHECK = os.path.join(HERE, "liblbm_gb300_check.so")  # -DLBM_CHECK_BOUNDS debug variant
-UNITS = ["lbm_kernels_n2.cu", "lbm_kernels_n3.cu", "lbm_kernels_n4.cu", "lbm_capi.cu"]
+UNITS = [f"lbm_kernels_n{n}_{p}.cu" for n in (2, 3, 4) for p in ("fp64", "fp32", "fp16s", "bf16s")] + ["lbm_capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -68,7 +68,7 @@ def build(force: bool = False, verbose: bool = False, check_bounds: bool = False
             raise RuntimeError(f"nvcc failed on {unit}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(UNITS), os.cpu_count() or 4)) as ex:
         results = list(ex.map(compile_one, UNITS))
     if verbose:
         for _, log in results:

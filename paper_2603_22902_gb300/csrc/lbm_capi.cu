@@ -20,8 +20,9 @@ struct lbm_handle {
     int diag_every = 0;
     int tile = TILE_32x8;
     KParams P{};
-    double* pop[2] = {nullptr, nullptr};  // 9 (N + 2) planes each
-    double* aux[2] = {nullptr, nullptr};  // 3 + 2N planes each
+    void* pop[2] = {nullptr, nullptr};    // one population set each (rest + moving block)
+    void* aux[2] = {nullptr, nullptr};    // 3 + 2N lagged planes each
+    size_t pop_bytes = 0, aux_bytes = 0;
     double* io = nullptr;                 // N + 6 planes: staging for host I/O
     double* diag_partial = nullptr;
     double* diag_out = nullptr;
@@ -34,6 +35,11 @@ struct lbm_handle {
 };
 
 static thread_local std::string g_create_error;
+
+namespace lbm {
+// Message of a failing call that has no handle (reported by lbm_last_error(NULL)).
+void set_handle_free_error(const char* msg) { g_create_error = msg; }
+}  // namespace lbm
 
 static int fail(lbm_handle* h, int code, const std::string& msg)
 {
@@ -52,10 +58,6 @@ static int cuda_fail(lbm_handle* h, cudaError_t e, const char* where)
         cudaError_t e_ = (call);                               \
         if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
     } while (0)
-
-// dispatch on the phase count
-#define LBM_DISPATCH_N(N_, CALL) \
-    ((N_) == 2 ? CALL(2) : (N_) == 3 ? CALL(3) : CALL(4))
 
 static size_t plane_bytes(const lbm_handle* h) { return (size_t)h->P.S * sizeof(double); }
 
@@ -85,8 +87,8 @@ int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_t
     if (grid->nx < 3 || grid->ny < 3) return fail(nullptr, LBM_EINVAL, "nx and ny must be >= 3");
     if ((long long)grid->nx * grid->ny > (1LL << 31)) return fail(nullptr, LBM_EINVAL, "grid too large");
     if (N < 2 || N > LBM_MAXN) return fail(nullptr, LBM_EINVAL, "N must be in [2, 4]");
-    if (num->precision != LBM_FP64)
-        return fail(nullptr, LBM_EINVAL, "precision not available in this build (LBM_FP64 only)");
+    if (num->precision < LBM_FP64 || num->precision > LBM_BF16S)
+        return fail(nullptr, LBM_EINVAL, "precision must be LBM_FP64, LBM_FP32, LBM_FP16S or LBM_BF16S");
     if (!(num->eps > 0.0) || !(num->mobility > 0.0)) return fail(nullptr, LBM_EINVAL, "eps and mobility must be > 0");
     if (num->diag_every < 0) return fail(nullptr, LBM_EINVAL, "diag_every must be >= 0");
     if (!(th->T_sol <= th->T_liq)) return fail(nullptr, LBM_EINVAL, "T_sol must be <= T_liq");
@@ -178,14 +180,21 @@ int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_t
     P.kg = 1.0 - 0.5 * P.omega_g;
 
     const size_t pb = plane_bytes(h);
-    const size_t npop = npop_planes(N), naux = naux_planes(N);
-    P.pop_elems = (long long)npop * P.S;
-    P.aux_elems = (long long)naux * P.S;
+    P.rest_elems = (long long)(N + 2) * P.S;
+    P.move_elems = 8LL * (N + 2) * P.S;
+    P.aux_elems = (long long)naux_planes(N) * P.S;
+    P.inv_E_ref = 1.0 / P.E_ref;
     P.dbg = nullptr;
+    dispatch(N, h->precision, [&](auto n, auto pr) {
+        using Pr = decltype(pr);
+        h->pop_bytes = (size_t)pop_set_bytes<Pr>(decltype(n)::value, P.S);
+        h->aux_bytes = (size_t)aux_set_bytes<Pr>(decltype(n)::value, P.S);
+        return 0;
+    });
     const int nb = diag_blocks(P.S);
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k) {
-        ok = cudaMalloc(&h->pop[k], npop * pb) == cudaSuccess && cudaMalloc(&h->aux[k], naux * pb) == cudaSuccess;
+        ok = cudaMalloc(&h->pop[k], h->pop_bytes) == cudaSuccess && cudaMalloc(&h->aux[k], h->aux_bytes) == cudaSuccess;
     }
     ok = ok && cudaMalloc(&h->io, (size_t)(N + 6) * pb) == cudaSuccess;
     ok = ok && cudaMalloc(&h->diag_partial, (size_t)nb * (2 * N + 2) * sizeof(double)) == cudaSuccess;
@@ -254,9 +263,9 @@ int lbm_set_fields(lbm_handle* h, const double* phi, const double* T, const doub
         }
     }
     h->cur = 0;
-#define LBM_CALL_INIT(NN) launch_init<NN>(h->P, dphi, dT, dux, duy, h->pop[0], h->aux[0], h->stream)
-    cudaError_t e = LBM_DISPATCH_N(h->N, LBM_CALL_INIT);
-#undef LBM_CALL_INIT
+    cudaError_t e = dispatch(h->N, h->precision, [&](auto n, auto pr) {
+        return launch_init<decltype(n)::value, decltype(pr)>(h->P, dphi, dT, dux, duy, h->pop[0], h->aux[0], h->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
     if (where == LBM_HOST) LBM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     h->ready = true;
@@ -266,9 +275,10 @@ int lbm_set_fields(lbm_handle* h, const double* phi, const double* T, const doub
 
 static int run_diag(lbm_handle* h, double* host_out)
 {
-#define LBM_CALL_DIAG(NN) launch_diag<NN>(h->P, h->pop[h->cur], h->aux[h->cur], h->diag_partial, h->diag_out, h->stream)
-    cudaError_t e = LBM_DISPATCH_N(h->N, LBM_CALL_DIAG);
-#undef LBM_CALL_DIAG
+    cudaError_t e = dispatch(h->N, h->precision, [&](auto n, auto pr) {
+        return launch_diag<decltype(n)::value, decltype(pr)>(h->P, h->pop[h->cur], h->aux[h->cur], h->diag_partial,
+                                                             h->diag_out, h->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics kernel");
     LBM_CUDA_TRY(h, cudaMemcpyAsync(host_out, h->diag_out, (2 * h->N + 2) * sizeof(double), cudaMemcpyDeviceToHost,
                                     h->stream));
@@ -284,9 +294,10 @@ int lbm_step(lbm_handle* h, long nsteps)
     LBM_CUDA_TRY(h, cudaSetDevice(h->device));
     for (long n = 0; n < nsteps; ++n) {
         const int a = h->cur, b = a ^ 1;
-#define LBM_CALL_STEP(NN) launch_step<NN>(h->P, h->pop[a], h->pop[b], h->aux[a], h->aux[b], h->tile, h->stream)
-        cudaError_t e = LBM_DISPATCH_N(h->N, LBM_CALL_STEP);
-#undef LBM_CALL_STEP
+        cudaError_t e = dispatch(h->N, h->precision, [&](auto n, auto pr) {
+            return launch_step<decltype(n)::value, decltype(pr)>(h->P, h->pop[a], h->pop[b], h->aux[a], h->aux[b],
+                                                                 h->tile, h->stream);
+        });
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
         h->cur = b;
         h->steps++;
@@ -319,10 +330,10 @@ int lbm_get_fields(lbm_handle* h, double* phi, double* T, double* H, double* fl,
             off += (k == 0 ? h->N : 1) * S;
         }
     }
-#define LBM_CALL_EXPORT(NN) \
-    launch_export<NN>(h->P, h->pop[h->cur], h->aux[h->cur], dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dev[6], h->stream)
-    cudaError_t e = LBM_DISPATCH_N(h->N, LBM_CALL_EXPORT);
-#undef LBM_CALL_EXPORT
+    cudaError_t e = dispatch(h->N, h->precision, [&](auto n, auto pr) {
+        return launch_export<decltype(n)::value, decltype(pr)>(h->P, h->pop[h->cur], h->aux[h->cur], dev[0], dev[1],
+                                                               dev[2], dev[3], dev[4], dev[5], dev[6], h->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(h, e, "export kernel");
     if (where == LBM_HOST) {
         for (int k = 0; k < 7; ++k)
@@ -356,8 +367,7 @@ int lbm_get_diagnostics(lbm_handle* h, lbm_diag* out)
 int lbm_save_state(lbm_handle* h, void* buf, size_t* bytes)
 {
     if (!h || !bytes) return fail(h, LBM_EINVAL, "NULL argument");
-    const size_t pb = plane_bytes(h);
-    const size_t need = sizeof(long long) + (npop_planes(h->N) + naux_planes(h->N)) * pb;
+    const size_t need = sizeof(long long) + h->pop_bytes + h->aux_bytes;
     if (!buf) {
         *bytes = need;
         return LBM_OK;
@@ -367,10 +377,10 @@ int lbm_save_state(lbm_handle* h, void* buf, size_t* bytes)
     LBM_CUDA_TRY(h, cudaSetDevice(h->device));
     char* b = (char*)buf;
     std::memcpy(b, &h->steps, sizeof(long long));
-    LBM_CUDA_TRY(h, cudaMemcpyAsync(b + sizeof(long long), h->pop[h->cur], npop_planes(h->N) * pb,
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(b + sizeof(long long), h->pop[h->cur], h->pop_bytes, cudaMemcpyDeviceToHost,
+                                    h->stream));
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(b + sizeof(long long) + h->pop_bytes, h->aux[h->cur], h->aux_bytes,
                                     cudaMemcpyDeviceToHost, h->stream));
-    LBM_CUDA_TRY(h, cudaMemcpyAsync(b + sizeof(long long) + npop_planes(h->N) * pb, h->aux[h->cur],
-                                    naux_planes(h->N) * pb, cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     *bytes = need;
     return LBM_OK;
@@ -379,18 +389,17 @@ int lbm_save_state(lbm_handle* h, void* buf, size_t* bytes)
 int lbm_load_state(lbm_handle* h, const void* buf, size_t bytes)
 {
     if (!h || !buf) return fail(h, LBM_EINVAL, "NULL argument");
-    const size_t pb = plane_bytes(h);
-    const size_t need = sizeof(long long) + (npop_planes(h->N) + naux_planes(h->N)) * pb;
+    const size_t need = sizeof(long long) + h->pop_bytes + h->aux_bytes;
     if (bytes != need) return fail(h, LBM_EINVAL, "state size does not match this handle");
     LBM_CUDA_TRY(h, cudaSetDevice(h->device));
     const char* b = (const char*)buf;
     long long steps;
     std::memcpy(&steps, b, sizeof(long long));
     h->cur = 0;
-    LBM_CUDA_TRY(h, cudaMemcpyAsync(h->pop[0], b + sizeof(long long), npop_planes(h->N) * pb, cudaMemcpyHostToDevice,
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(h->pop[0], b + sizeof(long long), h->pop_bytes, cudaMemcpyHostToDevice,
                                     h->stream));
-    LBM_CUDA_TRY(h, cudaMemcpyAsync(h->aux[0], b + sizeof(long long) + npop_planes(h->N) * pb,
-                                    naux_planes(h->N) * pb, cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(h->aux[0], b + sizeof(long long) + h->pop_bytes, h->aux_bytes,
+                                    cudaMemcpyHostToDevice, h->stream));
     LBM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     h->steps = steps;
     h->ready = true;

@@ -38,7 +38,9 @@ struct KParams {
     double tau_h_scale;           // 1 / (rho_ref c_p,ref c_s^2)
     double us[2], accel[2];
     double omega_g, kg;           // 1 / tau_g and 1 - 1/(2 tau_g), tau_g = M / c_s^2 + 1/2
-    long long pop_elems, aux_elems;  // sizes of one population set / one lagged set (elements)
+    long long rest_elems, move_elems; // elements of the rest / moving block of one population set
+    long long aux_elems;          // elements of one lagged set
+    double inv_E_ref;             // 1 / (rho_ref c_p,ref)
     unsigned long long* dbg;      // LBM_CHECK_BOUNDS builds: {violations, first site, first index}
 };
 
@@ -55,7 +57,13 @@ __device__ __forceinline__ bool lbm_in_bounds(unsigned long long* dbg, long long
     }
     return false;
 }
-#define LBM_LD(P_, ptr, idx, lim, site) (lbm_in_bounds((P_).dbg, (idx), (lim), (site)) ? __ldg((ptr) + (idx)) : 0.0)
+template <class T>
+__device__ __forceinline__ T lbm_zero_like(const T*)
+{
+    return static_cast<T>(0.0f);
+}
+#define LBM_LD(P_, ptr, idx, lim, site) \
+    (lbm_in_bounds((P_).dbg, (idx), (lim), (site)) ? __ldg((ptr) + (idx)) : lbm_zero_like(ptr))
 #define LBM_ST(P_, ptr, idx, lim, site, val)                                  \
     do {                                                                      \
         if (lbm_in_bounds((P_).dbg, (idx), (lim), (site))) (ptr)[idx] = (val); \

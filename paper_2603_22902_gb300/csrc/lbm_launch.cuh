@@ -1,14 +1,15 @@
 // lbm_launch.cuh -- host-side launchers of the device kernels, one explicit
-// instantiation set per phase count N (lbm_kernels_n{2,3,4}.cu).
+// instantiation set per phase count N and precision policy (lbm_kernels_*.cu).
 #pragma once
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lbm_device.cuh"
+#include "lbm_prec.cuh"
 
 namespace lbm {
-
-struct ExportPtrs;
 
 // Compiled tile shapes of the fused step kernel (TX x TY threads, one cell each).
 enum TileId { TILE_32x8 = 0, TILE_32x4 = 1, TILE_64x4 = 2, TILE_16x16 = 3, TILE_COUNT = 4 };
@@ -23,15 +24,15 @@ inline bool tile_dims(int id, int& tx, int& ty)
     }
 }
 
-template <int N>
-cudaError_t launch_step(const KParams& P, const double* pin, double* pout, const double* ain, double* aout,
-                        int tile, cudaStream_t st);
-template <int N>
-cudaError_t launch_export(const KParams& P, const double* pin, const double* ain, double* phi, double* T,
-                          double* H, double* fl, double* ux, double* uy, double* p, cudaStream_t st);
-template <int N>
+template <int N, class Pr>
+cudaError_t launch_step(const KParams& P, const void* pin, void* pout, const void* ain, void* aout, int tile,
+                        cudaStream_t st);
+template <int N, class Pr>
+cudaError_t launch_export(const KParams& P, const void* pin, const void* ain, double* phi, double* T, double* H,
+                          double* fl, double* ux, double* uy, double* p, cudaStream_t st);
+template <int N, class Pr>
 cudaError_t launch_init(const KParams& P, const double* phi, const double* T, const double* ux, const double* uy,
-                        double* pop, double* aux, cudaStream_t st);
+                        void* pop, void* aux, cudaStream_t st);
 // Two-pass deterministic reduction; partial must hold diag_blocks() * (2N + 2) doubles,
 // out 2N + 2 doubles (mass[N], solid[N], max |sum phi - 1|, non-finite count).
 constexpr int DIAG_NT = 256;
@@ -41,8 +42,26 @@ inline int diag_blocks(long long cells)
     if (b > 4 * 152) b = 4 * 152;  // a few blocks per SM of a GB300 is enough
     return (int)(b < 1 ? 1 : b);
 }
-template <int N>
-cudaError_t launch_diag(const KParams& P, const double* pop, const double* aux, double* partial, double* out,
+template <int N, class Pr>
+cudaError_t launch_diag(const KParams& P, const void* pop, const void* aux, double* partial, double* out,
                         cudaStream_t st);
+
+// Call f(std::integral_constant<int, N>{}, Prec{}) for the runtime phase count and
+// precision id (LBM_FP64 / FP32 / FP16S / BF16S = 0..3).
+template <class F>
+auto dispatch(int N, int prec, F&& f)
+{
+    auto byN = [&](auto pr) {
+        if (N == 2) return f(std::integral_constant<int, 2>{}, pr);
+        if (N == 3) return f(std::integral_constant<int, 3>{}, pr);
+        return f(std::integral_constant<int, 4>{}, pr);
+    };
+    switch (prec) {
+        case 1: return byN(PrecFP32{});
+        case 2: return byN(PrecFP16S{});
+        case 3: return byN(PrecBF16S{});
+        default: return byN(PrecFP64{});
+    }
+}
 
 }  // namespace lbm

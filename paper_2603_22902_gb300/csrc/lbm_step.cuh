@@ -1,15 +1,16 @@
-// lbm_step.cuh -- the fused FP64 time step of the coupled LB scheme
-// (arXiv 2603.22902, Section 3), one kernel launch per step.
+// lbm_step.cuh -- the fused time step of the coupled LB scheme (arXiv 2603.22902,
+// Section 3), one kernel launch per step, generic over the storage / arithmetic
+// precision policy (lbm_prec.cuh).
 //
-// State between launches: pre-collision (post-streaming) populations
-// f[9], g_p[9] (p < N), h[9] as structure-of-arrays planes, and the lagged planes
+// State between launches: pre-collision (post-streaming) populations f, g_p (p < N),
+// h as structure-of-arrays planes (rest block + moving block), and the lagged planes
 // mdot', Q' = rho c_p T mdot, psi', (phi_p u)'.  One launch reads set A and writes
 // set B (ping-pong), so it is race-free across blocks.
 //
 // Per block (a TX x TY tile, one thread per cell):
 //   1. each thread loads its cell's populations into registers and evaluates the
 //      moments (phi_p = sum g / (1 - mdot'/2), rho H = sum h + Q'/2), the mixture
-//      rule (eq. 2) and the enthalpy map (eq. H);
+//      rule (eq. 2) and the enthalpy map (eq. H, always FP64);
 //   2. the 1-cell halo ring recomputes phi_p, rho, psi of the neighbour cells from
 //      their own populations (no second kernel, no extra HBM field), and ghost
 //      values beyond walls/outflows are filled (zero gradient; wetting for phi_p);
@@ -20,9 +21,12 @@
 //   4. post-collision populations are pushed to the neighbours' slots of set B with
 //      the boundary rules (bounce-back, outflow copy, non-equilibrium extrapolation
 //      of the Dirichlet temperature), and the lagged planes are written.
+// No address outside the planes is ever formed, not even for a value that is then
+// not used: the compiler may issue loads ahead of the branch that guards them.
 #pragma once
 
 #include "lbm_device.cuh"
+#include "lbm_prec.cuh"
 
 namespace lbm {
 
@@ -37,43 +41,102 @@ __device__ __forceinline__ int wrap_index(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-// Stage A + B for a halo cell: phi_p, rho and psi only.
-template <int N>
-__device__ __forceinline__ void halo_moments(const KParams& P, const double* __restrict__ pin,
-                                             const double* __restrict__ ain, long long c,
-                                             double (&phi)[N], double& rho, double& psi)
+// Species kinds of the moving planes (their 16-bit encodings differ).
+constexpr int KIND_F = 0, KIND_G = 1, KIND_H = 2;
+
+// Views of one population set: rest block (N + 2 planes) and moving block (8 (N + 2)).
+template <class Pr>
+struct PopView {
+    typename Pr::TR* rest;
+    typename Pr::TM* move;
+};
+template <class Pr>
+__device__ __forceinline__ PopView<Pr> pop_view(const KParams& P, const void* base)
 {
+    char* b = (char*)base;
+    return PopView<Pr>{(typename Pr::TR*)b, (typename Pr::TM*)(b + P.rest_elems * (long long)sizeof(typename Pr::TR))};
+}
+
+// Load population i of species s at cell c (dequantised to R).
+template <class Pr, int KIND>
+__device__ __forceinline__ typename Pr::R ld_pop(const KParams& P, const PopView<Pr>& v, int s, int i, long long c, int site)
+{
+    using R = typename Pr::R;
+    if (i == 0) return (R)LBM_LD(P, v.rest, (long long)s * P.S + c, P.rest_elems, site);
+    const auto q = LBM_LD(P, v.move, (long long)(s * 8 + i - 1) * P.S + c, P.move_elems, site);
+    if constexpr (!Pr::QUANT) {
+        return (R)q;
+    } else {
+        const float w = (float)wgt(i);
+        const float qf = to_f(q);
+        if (KIND == KIND_F) return qf * (w * F_SCALE);
+        if (KIND == KIND_G) return qf * w;
+        return qf * (w * (float)P.E_ref);
+    }
+}
+
+// Store population i of species s at cell c (quantised from R).
+template <class Pr, int KIND>
+__device__ __forceinline__ void st_pop(const KParams& P, const PopView<Pr>& v, int s, int i, long long c,
+                                       typename Pr::R val, int site)
+{
+    using TM = typename Pr::TM;
+    if (i == 0) {
+        LBM_ST(P, v.rest, (long long)s * P.S + c, P.rest_elems, site, (typename Pr::TR)val);
+        return;
+    }
+    const long long idx = (long long)(s * 8 + i - 1) * P.S + c;
+    if constexpr (!Pr::QUANT) {
+        LBM_ST(P, v.move, idx, P.move_elems, site, (TM)val);
+    } else {
+        const float w = (float)wgt(i);
+        float q;
+        if (KIND == KIND_F) q = (float)val * (1.0f / (w * F_SCALE));
+        else if (KIND == KIND_G) q = (float)val * (1.0f / w);
+        else q = (float)val * (1.0f / w) * (float)P.inv_E_ref;
+        LBM_ST(P, v.move, idx, P.move_elems, site, from_f<TM>(q));
+    }
+}
+
+// Stage A + B for a halo cell: phi_p, rho and psi only (the map in FP64).
+template <int N, class Pr>
+__device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>& pin,
+                                             const typename Pr::TA* __restrict__ ain, long long c,
+                                             typename Pr::R (&phi)[N], typename Pr::R& rho, typename Pr::R& psi)
+{
+    using R = typename Pr::R;
     const long long S = P.S;
-    const double mdm = LBM_LD(P, ain, aux_mdot() * S + c, P.aux_elems, 1);
-    const double Qm = LBM_LD(P, ain, aux_Q() * S + c, P.aux_elems, 2);
-    const double den = 1.0 - 0.5 * mdm;
+    const R mdm = (R)LBM_LD(P, ain, aux_mdot() * S + c, P.aux_elems, 1);
+    const R Qm = (R)LBM_LD(P, ain, aux_Q() * S + c, P.aux_elems, 2);
+    const R den = R(1) - R(0.5) * mdm;
+    double phd[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) {
-        double s = 0.0;
+        R s = R(0);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s += LBM_LD(P, pin, plane_g(p, i) * S + c, P.pop_elems, 3);
+        for (int i = 0; i < 9; ++i) s += ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 3);
         phi[p] = s / den;
+        phd[p] = (double)phi[p];
     }
-    double sh = 0.0;
+    R sh = R(0);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) sh += LBM_LD(P, pin, plane_h(N, i) * S + c, P.pop_elems, 4);
-    const double rhoH = fma(0.5, Qm, sh);
-    const Mix<N> m = mixture_core<N>(P, phi);
+    for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 4);
+    const double rhoH = (double)rfma(R(0.5), Qm, sh);
+    const Mix<N> m = mixture_core<N>(P, phd);
     double fl, T;
     enthalpy_map<N, false>(P, m, rhoH, fl, T);
     const double fs = 1.0 - fl;
-    rho = fma(fs, m.rs, fl * m.rl);
-    psi = fs * m.dr;
+    rho = (R)fma(fs, m.rs, fl * m.rl);
+    psi = (R)(fs * m.dr);
 }
 
-// Push one post-collision population q_j of node (x, y) into set B.
+// Push one post-collision population q_j of species s at node (x, y) into set B.
 // Periodic sides wrap; a population leaving through an x wall is reflected into the
 // node's own opposite slot (half-way bounce-back); through a y wall likewise, except
 // the enthalpy populations at a Dirichlet wall (their incoming slots are filled by the
 // ghost rule); through an outflow side it is dropped.
-template <int J, bool IS_H>
-__device__ __forceinline__ void push(const KParams& P, double* __restrict__ pout, int plane, int plane_opp,
-                                     int x, int y, double q)
+template <int J, int KIND, class Pr>
+__device__ __forceinline__ void push(const KParams& P, const PopView<Pr>& out, int s, int x, int y, typename Pr::R q)
 {
     int tx = x + cx(J), ty = y + cy(J);
     bool xo = false, yo = false;
@@ -85,39 +148,69 @@ __device__ __forceinline__ void push(const KParams& P, double* __restrict__ pout
         if (P.bc[2] == PERIODIC) ty = ty < 0 ? ty + P.ny : ty - P.ny;
         else yo = true;
     }
+    const long long own = (long long)y * P.nx + x;
     if (!xo && !yo) {
-        LBM_ST(P, pout, plane * P.S + (long long)ty * P.nx + tx, P.pop_elems, 10, q);
+        st_pop<Pr, KIND>(P, out, s, J, (long long)ty * P.nx + tx, q, 10);
     } else if (xo) {
-        LBM_ST(P, pout, plane_opp * P.S + (long long)y * P.nx + x, P.pop_elems, 11, q);
+        st_pop<Pr, KIND>(P, out, s, opp(J), own, q, 11);
     } else {
         const int side = ty < 0 ? 2 : 3;
-        if (P.bc[side] == WALL && !(IS_H && P.tbc[side] == DIRICHLET))
-            LBM_ST(P, pout, plane_opp * P.S + (long long)y * P.nx + x, P.pop_elems, 12, q);
+        if (P.bc[side] == WALL && !(KIND == KIND_H && P.tbc[side] == DIRICHLET))
+            st_pop<Pr, KIND>(P, out, s, opp(J), own, q, 12);
     }
 }
 
 // Extra write of a boundary-row rule: value v into slot J of node (x + c_J, y),
 // same row; skipped when that node is beyond an x wall.
-template <int J>
-__device__ __forceinline__ void push_row(const KParams& P, double* __restrict__ pout, int plane, int x, int y, double v)
+template <int J, int KIND, class Pr>
+__device__ __forceinline__ void push_row(const KParams& P, const PopView<Pr>& out, int s, int x, int y,
+                                         typename Pr::R v)
 {
     int tx = x + cx(J);
     if (cx(J) != 0 && (unsigned)tx >= (unsigned)P.nx) {
         if (P.bc[0] != PERIODIC) return;
         tx = tx < 0 ? tx + P.nx : tx - P.nx;
     }
-    LBM_ST(P, pout, plane * P.S + (long long)y * P.nx + tx, P.pop_elems, 13, v);
+    st_pop<Pr, KIND>(P, out, s, J, (long long)y * P.nx + tx, v, 13);
 }
 
-template <int N, int TX, int TY, bool COLLIDE>
-__global__ void __launch_bounds__(TX * TY)
-fused_step_kernel(const KParams P, const double* __restrict__ pin, double* __restrict__ pout,
-                  const double* __restrict__ ain, double* __restrict__ aout, ExportPtrs ex)
+// All nine pushes of one species, plus the outflow copies of the boundary rows.
+template <int KIND, class Pr>
+__device__ __forceinline__ void push_species(const KParams& P, const PopView<Pr>& out, int s, int x, int y,
+                                             const typename Pr::R (&q)[9])
 {
+    push<0, KIND, Pr>(P, out, s, x, y, q[0]);
+    push<1, KIND, Pr>(P, out, s, x, y, q[1]);
+    push<2, KIND, Pr>(P, out, s, x, y, q[2]);
+    push<3, KIND, Pr>(P, out, s, x, y, q[3]);
+    push<4, KIND, Pr>(P, out, s, x, y, q[4]);
+    push<5, KIND, Pr>(P, out, s, x, y, q[5]);
+    push<6, KIND, Pr>(P, out, s, x, y, q[6]);
+    push<7, KIND, Pr>(P, out, s, x, y, q[7]);
+    push<8, KIND, Pr>(P, out, s, x, y, q[8]);
+    if (y == 0 && P.bc[2] == OUTFLOW) {
+        push_row<2, KIND, Pr>(P, out, s, x, y, q[2]);
+        push_row<5, KIND, Pr>(P, out, s, x, y, q[5]);
+        push_row<6, KIND, Pr>(P, out, s, x, y, q[6]);
+    }
+    if (y == P.ny - 1 && P.bc[3] == OUTFLOW) {
+        push_row<4, KIND, Pr>(P, out, s, x, y, q[4]);
+        push_row<7, KIND, Pr>(P, out, s, x, y, q[7]);
+        push_row<8, KIND, Pr>(P, out, s, x, y, q[8]);
+    }
+}
+
+template <int N, int TX, int TY, bool COLLIDE, class Pr>
+__global__ void __launch_bounds__(TX * TY)
+fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __restrict__ pout_base,
+                  const typename Pr::TA* __restrict__ ain, typename Pr::TA* __restrict__ aout, ExportPtrs ex)
+{
+    using R = typename Pr::R;
+    using TA = typename Pr::TA;
     constexpr int W = TX + 2, H = TY + 2, NT = TX * TY, NRING = 2 * W + 2 * TY;
-    __shared__ double s_phi[N][H][W];
-    __shared__ double s_rho[H][W];
-    __shared__ double s_psi[H][W];
+    __shared__ R s_phi[N][H][W];
+    __shared__ R s_rho[H][W];
+    __shared__ R s_psi[H][W];
 
     const int nx = P.nx, ny = P.ny;
     const long long S = P.S;
@@ -127,8 +220,8 @@ fused_step_kernel(const KParams P, const double* __restrict__ pin, double* __res
     const int x = x0 + tx, y = y0 + ty;
     const bool owned = x < nx && y < ny;
     const bool xper = P.bc[0] == PERIODIC, yper = P.bc[2] == PERIODIC;
+    const PopView<Pr> pin = pop_view<Pr>(P, pin_base);
 
-    // halo position (lx, ly) of the tile: recompute the neighbour's moments
     // The cell coordinates are brought into range before anything else (periodic:
     // full modulo, since a tile may be wider / taller than the domain; otherwise:
     // clamped), so no address outside the planes is ever formed, even for a position
@@ -145,8 +238,8 @@ fused_step_kernel(const KParams P, const double* __restrict__ pin, double* __res
             else { beyond = true; gy = min(max(gy, 0), ny - 1); }
         }
         if (beyond) return;
-        double ph[N], r, ps;
-        halo_moments<N>(P, pin, ain, (long long)gy * nx + gx, ph, r, ps);
+        R ph[N], r, ps;
+        halo_moments<N, Pr>(P, pin, ain, (long long)gy * nx + gx, ph, r, ps);
 #pragma unroll
         for (int p = 0; p < N; ++p) s_phi[p][ly][lx] = ph[p];
         s_rho[ly][lx] = r;
@@ -154,52 +247,58 @@ fused_step_kernel(const KParams P, const double* __restrict__ pin, double* __res
     };
 
     // ---- stage A + B of the own cell --------------------------------------
-    double f[9], g[N][9], h[9];
-    double phi[N], rhoH = 0.0, fl = 1.0, T = 0.0, rho = 1.0, mu = 0.0, lam = 0.0, cp = 1.0, psi = 0.0, chi = 0.0;
+    R f[9], g[N][9], h[9];
+    R phi[N], rhoH = R(0), fl = R(1), T = R(0), rho = R(1), mu = R(0), lam = R(0), cp = R(1), psi = R(0), chi = R(0);
     // every thread keeps an in-range cell index: loads under `if (owned)` may be
     // issued speculatively, so a thread outside the domain must not form an address
     // past the end of the planes
     const long long c = owned ? (long long)y * nx + x : 0;
     if (owned) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = LBM_LD(P, pin, plane_f(i) * S + c, P.pop_elems, 5);
+        for (int i = 0; i < 9; ++i) f[i] = ld_pop<Pr, KIND_F>(P, pin, 0, i, c, 5);
 #pragma unroll
         for (int p = 0; p < N; ++p)
 #pragma unroll
-            for (int i = 0; i < 9; ++i) g[p][i] = LBM_LD(P, pin, plane_g(p, i) * S + c, P.pop_elems, 6);
+            for (int i = 0; i < 9; ++i) g[p][i] = ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 6);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) h[i] = LBM_LD(P, pin, plane_h(N, i) * S + c, P.pop_elems, 7);
-        const double mdm = LBM_LD(P, ain, aux_mdot() * S + c, P.aux_elems, 8);
-        const double Qm = LBM_LD(P, ain, aux_Q() * S + c, P.aux_elems, 9);
-        const double den = 1.0 - 0.5 * mdm;
+        for (int i = 0; i < 9; ++i) h[i] = ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 7);
+        const R mdm = (R)LBM_LD(P, ain, aux_mdot() * S + c, P.aux_elems, 8);
+        const R Qm = (R)LBM_LD(P, ain, aux_Q() * S + c, P.aux_elems, 9);
+        const R den = R(1) - R(0.5) * mdm;
+        double phd[N];
 #pragma unroll
         for (int p = 0; p < N; ++p) {
-            double s = 0.0;
+            R s = R(0);
 #pragma unroll
             for (int i = 0; i < 9; ++i) s += g[p][i];
             phi[p] = s / den;
+            phd[p] = (double)phi[p];
         }
-        double sh = 0.0;
+        R sh = R(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) sh += h[i];
-        rhoH = fma(0.5, Qm, sh);
-        const Mix<N> m = mixture_core<N>(P, phi);
-        enthalpy_map<N, true>(P, m, rhoH, fl, T);
-        const double fs = 1.0 - fl;
+        rhoH = rfma(R(0.5), Qm, sh);
+        // eq. 2 + eq. H in FP64
+        const Mix<N> m = mixture_core<N>(P, phd);
+        double fld, Td;
+        enthalpy_map<N, true>(P, m, (double)rhoH, fld, Td);
+        const double fs = 1.0 - fld;
         double ms = 0.0, ml = 0.0, ks = 0.0, kl = 0.0;
 #pragma unroll
         for (int p = 0; p < N; ++p) {
-            ms = fma(phi[p], P.mu_s[p], ms);
-            ml = fma(phi[p], P.mu_l[p], ml);
-            ks = fma(phi[p], P.lam_s[p], ks);
-            kl = fma(phi[p], P.lam_l[p], kl);
+            ms = fma(phd[p], P.mu_s[p], ms);
+            ml = fma(phd[p], P.mu_l[p], ml);
+            ks = fma(phd[p], P.lam_s[p], ks);
+            kl = fma(phd[p], P.lam_l[p], kl);
         }
-        rho = fma(fs, m.rs, fl * m.rl);
-        mu = fma(fs, ms, fl * ml);
-        lam = fma(fs, ks, fl * kl);
-        cp = fma(fs, m.cs, fl * m.cl);
-        psi = fs * m.dr;
-        chi = fs * m.pcm;
+        fl = (R)fld;
+        T = (R)Td;
+        rho = (R)fma(fs, m.rs, fld * m.rl);
+        mu = (R)fma(fs, ms, fld * ml);
+        lam = (R)fma(fs, ks, fld * kl);
+        cp = (R)fma(fs, m.cs, fld * m.cl);
+        psi = (R)(fs * m.dr);
+        chi = (R)(fs * m.pcm);
 #pragma unroll
         for (int p = 0; p < N; ++p) s_phi[p][ty + 1][tx + 1] = phi[p];
         s_rho[ty + 1][tx + 1] = rho;
@@ -228,19 +327,19 @@ fused_step_kernel(const KParams P, const double* __restrict__ pin, double* __res
         const int sy = yo ? min(max(gy, 0), ny - 1) - y0 + 1 : ly;
         const int wx = xo ? (gx < 0 ? 0 : 1) : -1;
         const int wy = yo ? (gy < 0 ? 2 : 3) : -1;
-        double ph[N];
+        R ph[N];
 #pragma unroll
         for (int p = 0; p < N; ++p) ph[p] = s_phi[p][sy][sx];
 #pragma unroll
         for (int p = 0; p < N; ++p) {
-            double corr = 0.0;
+            R corr = R(0);
 #pragma unroll
             for (int q = 0; q < N; ++q) {
                 if (q == p) continue;
                 double cw = 0.0;
                 if (wx >= 0) cw += P.wet[wx][p][q];
                 if (wy >= 0) cw += P.wet[wy][p][q];
-                corr = fma(cw * ph[p], ph[q], corr);
+                corr = rfma((R)cw * ph[p], ph[q], corr);
             }
             s_phi[p][ly][lx] = ph[p] + corr;
         }
@@ -252,114 +351,121 @@ fused_step_kernel(const KParams P, const double* __restrict__ pin, double* __res
 
     // ---- stage C: isotropic stencils ---------------------------------------
     const int lx = tx + 1, ly = ty + 1;
-    double gpx[N], gpy[N], lap[N];
-    auto grad = [&](double (*a)[W], double& gx_, double& gy_) {
-        const double e = a[ly][lx + 1], w = a[ly][lx - 1], n = a[ly + 1][lx], s = a[ly - 1][lx];
-        const double ne = a[ly + 1][lx + 1], nw = a[ly + 1][lx - 1], se = a[ly - 1][lx + 1], sw = a[ly - 1][lx - 1];
-        gx_ = (e - w) * (1.0 / 3.0) + ((ne - nw) + (se - sw)) * (1.0 / 12.0);
-        gy_ = (n - s) * (1.0 / 3.0) + ((ne - se) + (nw - sw)) * (1.0 / 12.0);
+    R gpx[N], gpy[N], lap[N];
+    auto grad = [&](R (*a)[W], R& gx_, R& gy_) {
+        const R e = a[ly][lx + 1], w = a[ly][lx - 1], n = a[ly + 1][lx], s = a[ly - 1][lx];
+        const R ne = a[ly + 1][lx + 1], nw = a[ly + 1][lx - 1], se = a[ly - 1][lx + 1], sw = a[ly - 1][lx - 1];
+        gx_ = (e - w) * R(1.0 / 3.0) + ((ne - nw) + (se - sw)) * R(1.0 / 12.0);
+        gy_ = (n - s) * R(1.0 / 3.0) + ((ne - se) + (nw - sw)) * R(1.0 / 12.0);
     };
 #pragma unroll
     for (int p = 0; p < N; ++p) {
-        double (*a)[W] = s_phi[p];
+        R (*a)[W] = s_phi[p];
         grad(a, gpx[p], gpy[p]);
-        const double v0 = a[ly][lx];
-        const double ax = (a[ly][lx + 1] + a[ly][lx - 1]) + (a[ly + 1][lx] + a[ly - 1][lx]);
-        const double dg = (a[ly + 1][lx + 1] + a[ly + 1][lx - 1]) + (a[ly - 1][lx + 1] + a[ly - 1][lx - 1]);
-        lap[p] = ax * (2.0 / 3.0) + dg * (1.0 / 6.0) - v0 * (10.0 / 3.0);
+        const R v0 = a[ly][lx];
+        const R ax = (a[ly][lx + 1] + a[ly][lx - 1]) + (a[ly + 1][lx] + a[ly - 1][lx]);
+        const R dg = (a[ly + 1][lx + 1] + a[ly + 1][lx - 1]) + (a[ly - 1][lx + 1] + a[ly - 1][lx - 1]);
+        lap[p] = ax * R(2.0 / 3.0) + dg * R(1.0 / 6.0) - v0 * R(10.0 / 3.0);
     }
-    double grx, gry, gsx, gsy;
+    R grx, gry, gsx, gsy;
     grad(s_rho, grx, gry);
     grad(s_psi, gsx, gsy);
 
     // ---- stage D: pairwise normals, R_p, chemical potentials, F_s -----------
-    double Rx[N], Ry[N], mup[N], gpv[N];
+    R Rx[N], Ry[N], mup[N], gpv[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) {
-        Rx[p] = 0.0;
-        Ry[p] = 0.0;
-        mup[p] = 0.0;
-        gpv[p] = gprime(phi[p]);
+        Rx[p] = R(0);
+        Ry[p] = R(0);
+        mup[p] = R(0);
+        gpv[p] = R(2) * phi[p] * (R(1) - phi[p]) * (R(1) - R(2) * phi[p]);  // g'(phi), g = phi^2 (1 - phi)^2
     }
 #pragma unroll
     for (int p = 0; p < N; ++p)
 #pragma unroll
         for (int q = p + 1; q < N; ++q) {
-            const double s = phi[p] + phi[q];
-            double nxv = 0.0, nyv = 0.0;
-            if (s > 1e-12) {
-                const double is2 = 1.0 / (s * s);
-                const double Gx = (phi[q] * gpx[p] - phi[p] * gpx[q]) * is2;
-                const double Gy = (phi[q] * gpy[p] - phi[p] * gpy[q]) * is2;
-                const double G2 = Gx * Gx + Gy * Gy;
-                if (G2 > 1e-24) {
-                    const double r = rsqrt(G2);
+            const R s = phi[p] + phi[q];
+            R nxv = R(0), nyv = R(0);
+            if (s > R(1e-12)) {
+                const R is2 = R(1) / (s * s);
+                const R Gx = (phi[q] * gpx[p] - phi[p] * gpx[q]) * is2;
+                const R Gy = (phi[q] * gpy[p] - phi[p] * gpy[q]) * is2;
+                const R G2 = Gx * Gx + Gy * Gy;
+                bool ok = G2 > R(Pr::NABS2);
+                if constexpr (Pr::NGUARD > 0.0f) {
+                    const R ref = (phi[q] * phi[q] * (gpx[p] * gpx[p] + gpy[p] * gpy[p]) +
+                                   phi[p] * phi[p] * (gpx[q] * gpx[q] + gpy[q] * gpy[q])) * (is2 * is2);
+                    ok = ok && G2 > R(Pr::NGUARD * Pr::NGUARD) * ref;
+                }
+                if (ok) {
+                    const R r = rrsqrt(G2);
                     nxv = Gx * r;
                     nyv = Gy * r;
                 }
             }
-            const double a = P.four_eps * phi[p] * phi[q];
-            Rx[p] = fma(a, nxv, Rx[p]);
-            Ry[p] = fma(a, nyv, Ry[p]);
-            Rx[q] = fma(-a, nxv, Rx[q]);
-            Ry[q] = fma(-a, nyv, Ry[q]);
-            const double gs = gprime(s);
-            mup[p] += fma(P.b2[p][q], gpv[p] - gs, P.kk[p][q] * lap[q]);
-            mup[q] += fma(P.b2[q][p], gpv[q] - gs, P.kk[q][p] * lap[p]);
+            const R a = (R)P.four_eps * phi[p] * phi[q];
+            Rx[p] = rfma(a, nxv, Rx[p]);
+            Ry[p] = rfma(a, nyv, Ry[p]);
+            Rx[q] = rfma(-a, nxv, Rx[q]);
+            Ry[q] = rfma(-a, nyv, Ry[q]);
+            const R gs = R(2) * s * (R(1) - s) * (R(1) - R(2) * s);
+            mup[p] += rfma((R)P.b2[p][q], gpv[p] - gs, (R)P.kk[p][q] * lap[q]);
+            mup[q] += rfma((R)P.b2[q][p], gpv[q] - gs, (R)P.kk[q][p] * lap[p]);
         }
-    double Fx = rho * P.accel[0], Fy = rho * P.accel[1];
+    R Fx = rho * (R)P.accel[0], Fy = rho * (R)P.accel[1];
 #pragma unroll
     for (int p = 0; p < N; ++p) {
-        Fx = fma(mup[p], gpx[p], Fx);
-        Fy = fma(mup[p], gpy[p], Fy);
+        Fx = rfma(mup[p], gpx[p], Fx);
+        Fy = rfma(mup[p], gpy[p], Fy);
     }
 
     // ---- stage E: flow macroscopics ----------------------------------------
-    const double jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
-    const double jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
-    const double sum_f = ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
-    const double irho = 1.0 / rho;
-    const double usx = fma(0.5, Fx, jx) * irho, usy = fma(0.5, Fy, jy) * irho;
-    const double fpx = chi * (P.us[0] - usx), fpy = chi * (P.us[1] - usy);
-    const double ux = fma(0.5, fpx, usx), uy = fma(0.5, fpy, usy);
-    const double psim = LBM_LD(P, ain, aux_psi() * S + c, P.aux_elems, 14);
-    const double mdot = -((psi - psim) + (ux * gsx + uy * gsy)) * irho;
-    const double Ssrc = fma(rho, mdot, ux * grx + uy * gry);
-    const double Lxx = fma(2.0 * ux, Fx, Ssrc * (1.0 / 3.0));
-    const double Lyy = fma(2.0 * uy, Fy, Ssrc * (1.0 / 3.0));
-    const double Lxy = fma(ux, Fy, uy * Fx);
-    const double tau_f = fma(3.0 * mu, irho, 0.5);
-    const double F0 = wgt(0) * fma(-1.5, Lxx + Lyy, Ssrc);
-    const double uu = fma(ux, ux, uy * uy);
-    const double p = 0.6 * (((sum_f + 0.5 * Ssrc) + (tau_f - 0.5) * F0) - rho * wgt(0) * 1.5 * uu);
+    const R jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
+    const R jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
+    const R sum_f = ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
+    const R irho = R(1) / rho;
+    const R usx = rfma(R(0.5), Fx, jx) * irho, usy = rfma(R(0.5), Fy, jy) * irho;
+    const R fpx = chi * ((R)P.us[0] - usx), fpy = chi * ((R)P.us[1] - usy);
+    const R ux = rfma(R(0.5), fpx, usx), uy = rfma(R(0.5), fpy, usy);
+    const R psim = (R)LBM_LD(P, ain, aux_psi() * S + c, P.aux_elems, 14);
+    const R mdot = -((psi - psim) + (ux * gsx + uy * gsy)) * irho;
+    const R Ssrc = rfma(rho, mdot, ux * grx + uy * gry);
+    const R Lxx = rfma(R(2) * ux, Fx, Ssrc * R(1.0 / 3.0));
+    const R Lyy = rfma(R(2) * uy, Fy, Ssrc * R(1.0 / 3.0));
+    const R Lxy = rfma(ux, Fy, uy * Fx);
+    const R tau_f = rfma(R(3) * mu, irho, R(0.5));
+    const R F0 = R(wgt(0)) * rfma(R(-1.5), Lxx + Lyy, Ssrc);
+    const R uu = rfma(ux, ux, uy * uy);
+    const R p = R(0.6) * (((sum_f + R(0.5) * Ssrc) + (tau_f - R(0.5)) * F0) - rho * R(wgt(0)) * R(1.5) * uu);
 
     if (!COLLIDE) {
 #pragma unroll
         for (int q = 0; q < N; ++q)
-            if (ex.phi) LBM_ST(P, ex.phi, q * S + c, N * S, 20, phi[q]);
-        if (ex.T) LBM_ST(P, ex.T, c, S, 21, T);
-        if (ex.H) LBM_ST(P, ex.H, c, S, 22, rhoH * irho);
-        if (ex.fl) LBM_ST(P, ex.fl, c, S, 23, fl);
-        if (ex.ux) LBM_ST(P, ex.ux, c, S, 24, ux);
-        if (ex.uy) LBM_ST(P, ex.uy, c, S, 25, uy);
-        if (ex.p) LBM_ST(P, ex.p, c, S, 26, p);
+            if (ex.phi) LBM_ST(P, ex.phi, q * S + c, N * S, 20, (double)phi[q]);
+        if (ex.T) LBM_ST(P, ex.T, c, S, 21, (double)T);
+        if (ex.H) LBM_ST(P, ex.H, c, S, 22, (double)(rhoH * irho));
+        if (ex.fl) LBM_ST(P, ex.fl, c, S, 23, (double)fl);
+        if (ex.ux) LBM_ST(P, ex.ux, c, S, 24, (double)ux);
+        if (ex.uy) LBM_ST(P, ex.uy, c, S, 25, (double)uy);
+        if (ex.p) LBM_ST(P, ex.p, c, S, 26, (double)p);
         return;
     }
+    const PopView<Pr> pout = pop_view<Pr>(P, pout_base);
 
     // ---- stage F: flow collision -------------------------------------------
     {
-        const double om = 1.0 / tau_f, k = fma(-0.5, om, 1.0), om1 = 1.0 - om;
-        const double Fex = fma(rho, fpx, Fx), Fey = fma(rho, fpy, Fy);
-        const double rom = om * rho;
-        const double a0 = om * fma(-1.5 * rho, uu, 3.0 * p) + k * fma(-1.5, Lxx + Lyy, Ssrc);
-        const double ax = 3.0 * fma(rom, ux, k * Fex);
-        const double ay = 3.0 * fma(rom, uy, k * Fey);
-        const double axx = 4.5 * fma(rom * ux, ux, k * Lxx);
-        const double ayy = 4.5 * fma(rom * uy, uy, k * Lyy);
-        const double axy = 9.0 * fma(rom * ux, uy, k * Lxy);
-        const double bx = a0 + axx, by = a0 + ayy, bd = a0 + axx + ayy;
-        double X[9];
-        X[0] = fma(-6.75 * om, p, a0);
+        const R om = R(1) / tau_f, k = rfma(R(-0.5), om, R(1)), om1 = R(1) - om;
+        const R Fex = rfma(rho, fpx, Fx), Fey = rfma(rho, fpy, Fy);
+        const R rom = om * rho;
+        const R a0 = om * rfma(R(-1.5) * rho, uu, R(3) * p) + k * rfma(R(-1.5), Lxx + Lyy, Ssrc);
+        const R ax = R(3) * rfma(rom, ux, k * Fex);
+        const R ay = R(3) * rfma(rom, uy, k * Fey);
+        const R axx = R(4.5) * rfma(rom * ux, ux, k * Lxx);
+        const R ayy = R(4.5) * rfma(rom * uy, uy, k * Lyy);
+        const R axy = R(9) * rfma(rom * ux, uy, k * Lxy);
+        const R bx = a0 + axx, by = a0 + ayy, bd = a0 + axx + ayy;
+        R X[9];
+        X[0] = rfma(R(-6.75) * om, p, a0);
         X[1] = bx + ax;
         X[3] = bx - ax;
         X[2] = by + ay;
@@ -368,121 +474,86 @@ fused_step_kernel(const KParams P, const double* __restrict__ pin, double* __res
         X[7] = (bd + axy) - (ax + ay);
         X[6] = (bd - axy) + (ay - ax);
         X[8] = (bd - axy) - (ay - ax);
-        double q[9];
+        R q[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) q[i] = fma(wgt(i), X[i], om1 * f[i]);
-#define LBM_PUSH_F(J) push<J, false>(P, pout, plane_f(J), plane_f(opp(J)), x, y, q[J]);
-        LBM_PUSH_F(0) LBM_PUSH_F(1) LBM_PUSH_F(2) LBM_PUSH_F(3) LBM_PUSH_F(4)
-        LBM_PUSH_F(5) LBM_PUSH_F(6) LBM_PUSH_F(7) LBM_PUSH_F(8)
-#undef LBM_PUSH_F
-        if (y == 0 && P.bc[2] == OUTFLOW) {
-            push_row<2>(P, pout, plane_f(2), x, y, q[2]);
-            push_row<5>(P, pout, plane_f(5), x, y, q[5]);
-            push_row<6>(P, pout, plane_f(6), x, y, q[6]);
-        }
-        if (y == ny - 1 && P.bc[3] == OUTFLOW) {
-            push_row<4>(P, pout, plane_f(4), x, y, q[4]);
-            push_row<7>(P, pout, plane_f(7), x, y, q[7]);
-            push_row<8>(P, pout, plane_f(8), x, y, q[8]);
-        }
+        for (int i = 0; i < 9; ++i) q[i] = rfma(R(wgt(i)), X[i], om1 * f[i]);
+        push_species<KIND_F, Pr>(P, pout, 0, x, y, q);
     }
 
     // ---- stage F: phase-field collisions -------------------------------------
     {
-        const double og = P.omega_g, kg = P.kg, og1 = 1.0 - og;
+        const R og = (R)P.omega_g, kg = (R)P.kg, og1 = R(1) - og;
 #pragma unroll
         for (int pp = 0; pp < N; ++pp) {
-            const double Dx = phi[pp] * ux - LBM_LD(P, ain, aux_phiux(pp) * S + c, P.aux_elems, 15);
-            const double Dy = phi[pp] * uy - LBM_LD(P, ain, aux_phiuy(N, pp) * S + c, P.aux_elems, 16);
-            const double b0 = og * phi[pp] + kg * phi[pp] * mdot;
-            const double bxv = 3.0 * og * phi[pp] * ux + kg * fma(3.0, Dx, Rx[pp]);
-            const double byv = 3.0 * og * phi[pp] * uy + kg * fma(3.0, Dy, Ry[pp]);
-            double q[9];
-            q[0] = fma(wgt(0), b0, og1 * g[pp][0]);
-            q[1] = fma(wgt(1), b0 + bxv, og1 * g[pp][1]);
-            q[3] = fma(wgt(3), b0 - bxv, og1 * g[pp][3]);
-            q[2] = fma(wgt(2), b0 + byv, og1 * g[pp][2]);
-            q[4] = fma(wgt(4), b0 - byv, og1 * g[pp][4]);
-            q[5] = fma(wgt(5), b0 + (bxv + byv), og1 * g[pp][5]);
-            q[7] = fma(wgt(7), b0 - (bxv + byv), og1 * g[pp][7]);
-            q[6] = fma(wgt(6), b0 + (byv - bxv), og1 * g[pp][6]);
-            q[8] = fma(wgt(8), b0 - (byv - bxv), og1 * g[pp][8]);
-#define LBM_PUSH_G(J) push<J, false>(P, pout, plane_g(pp, J), plane_g(pp, opp(J)), x, y, q[J]);
-            LBM_PUSH_G(0) LBM_PUSH_G(1) LBM_PUSH_G(2) LBM_PUSH_G(3) LBM_PUSH_G(4)
-            LBM_PUSH_G(5) LBM_PUSH_G(6) LBM_PUSH_G(7) LBM_PUSH_G(8)
-#undef LBM_PUSH_G
-            if (y == 0 && P.bc[2] == OUTFLOW) {
-                push_row<2>(P, pout, plane_g(pp, 2), x, y, q[2]);
-                push_row<5>(P, pout, plane_g(pp, 5), x, y, q[5]);
-                push_row<6>(P, pout, plane_g(pp, 6), x, y, q[6]);
-            }
-            if (y == ny - 1 && P.bc[3] == OUTFLOW) {
-                push_row<4>(P, pout, plane_g(pp, 4), x, y, q[4]);
-                push_row<7>(P, pout, plane_g(pp, 7), x, y, q[7]);
-                push_row<8>(P, pout, plane_g(pp, 8), x, y, q[8]);
-            }
-            LBM_ST(P, aout, aux_phiux(pp) * S + c, P.aux_elems, 30, phi[pp] * ux);
-            LBM_ST(P, aout, aux_phiuy(N, pp) * S + c, P.aux_elems, 31, phi[pp] * uy);
+            const R Dx = phi[pp] * ux - (R)LBM_LD(P, ain, aux_phiux(pp) * S + c, P.aux_elems, 15);
+            const R Dy = phi[pp] * uy - (R)LBM_LD(P, ain, aux_phiuy(N, pp) * S + c, P.aux_elems, 16);
+            const R b0 = og * phi[pp] + kg * phi[pp] * mdot;
+            const R bxv = R(3) * og * phi[pp] * ux + kg * rfma(R(3), Dx, Rx[pp]);
+            const R byv = R(3) * og * phi[pp] * uy + kg * rfma(R(3), Dy, Ry[pp]);
+            R q[9];
+            q[0] = rfma(R(wgt(0)), b0, og1 * g[pp][0]);
+            q[1] = rfma(R(wgt(1)), b0 + bxv, og1 * g[pp][1]);
+            q[3] = rfma(R(wgt(3)), b0 - bxv, og1 * g[pp][3]);
+            q[2] = rfma(R(wgt(2)), b0 + byv, og1 * g[pp][2]);
+            q[4] = rfma(R(wgt(4)), b0 - byv, og1 * g[pp][4]);
+            q[5] = rfma(R(wgt(5)), b0 + (bxv + byv), og1 * g[pp][5]);
+            q[7] = rfma(R(wgt(7)), b0 - (bxv + byv), og1 * g[pp][7]);
+            q[6] = rfma(R(wgt(6)), b0 + (byv - bxv), og1 * g[pp][6]);
+            q[8] = rfma(R(wgt(8)), b0 - (byv - bxv), og1 * g[pp][8]);
+            push_species<KIND_G, Pr>(P, pout, 1 + pp, x, y, q);
+            LBM_ST(P, aout, aux_phiux(pp) * S + c, P.aux_elems, 30, (TA)(phi[pp] * ux));
+            LBM_ST(P, aout, aux_phiuy(N, pp) * S + c, P.aux_elems, 31, (TA)(phi[pp] * uy));
         }
     }
 
     // ---- stage F: enthalpy collision + Dirichlet ghosts ---------------------
     {
-        const double Z = rho * cp * T, E = P.E_ref * T;
-        const double oh = 1.0 / fma(lam, P.tau_h_scale, 0.5), kh = fma(-0.5, oh, 1.0), oh1 = 1.0 - oh;
-        const double Zm = Z * mdot;
-        const double c0 = oh * fma(-1.5 * Z, uu, E) + kh * Zm;
-        const double ohZ = oh * Z;
-        const double cxv = 3.0 * ohZ * ux, cyv = 3.0 * ohZ * uy;
-        const double cxx = 4.5 * ohZ * ux * ux, cyy = 4.5 * ohZ * uy * uy, cxy = 9.0 * ohZ * ux * uy;
-        const double heq0 = (rhoH - E) + wgt(0) * fma(-1.5 * Z, uu, E);
-        const double bx = c0 + cxx, by = c0 + cyy, bd = c0 + cxx + cyy;
-        double q[9];
-        q[0] = fma(oh, heq0, fma(kh * wgt(0), Zm, oh1 * h[0]));
-        q[1] = fma(wgt(1), bx + cxv, oh1 * h[1]);
-        q[3] = fma(wgt(3), bx - cxv, oh1 * h[3]);
-        q[2] = fma(wgt(2), by + cyv, oh1 * h[2]);
-        q[4] = fma(wgt(4), by - cyv, oh1 * h[4]);
-        q[5] = fma(wgt(5), (bd + cxy) + (cxv + cyv), oh1 * h[5]);
-        q[7] = fma(wgt(7), (bd + cxy) - (cxv + cyv), oh1 * h[7]);
-        q[6] = fma(wgt(6), (bd - cxy) + (cyv - cxv), oh1 * h[6]);
-        q[8] = fma(wgt(8), (bd - cxy) - (cyv - cxv), oh1 * h[8]);
-#define LBM_PUSH_H(J) push<J, true>(P, pout, plane_h(N, J), plane_h(N, opp(J)), x, y, q[J]);
-        LBM_PUSH_H(0) LBM_PUSH_H(1) LBM_PUSH_H(2) LBM_PUSH_H(3) LBM_PUSH_H(4)
-        LBM_PUSH_H(5) LBM_PUSH_H(6) LBM_PUSH_H(7) LBM_PUSH_H(8)
-#undef LBM_PUSH_H
+        const R Z = rho * cp * T, E = (R)P.E_ref * T;
+        const R oh = R(1) / rfma(lam, (R)P.tau_h_scale, R(0.5)), kh = rfma(R(-0.5), oh, R(1)), oh1 = R(1) - oh;
+        const R Zm = Z * mdot;
+        const R c0 = oh * rfma(R(-1.5) * Z, uu, E) + kh * Zm;
+        const R ohZ = oh * Z;
+        const R cxv = R(3) * ohZ * ux, cyv = R(3) * ohZ * uy;
+        const R cxx = R(4.5) * ohZ * ux * ux, cyy = R(4.5) * ohZ * uy * uy, cxy = R(9) * ohZ * ux * uy;
+        const R heq0 = (rhoH - E) + R(wgt(0)) * rfma(R(-1.5) * Z, uu, E);
+        const R bx = c0 + cxx, by = c0 + cyy, bd = c0 + cxx + cyy;
+        R q[9];
+        q[0] = rfma(oh, heq0, rfma(kh * R(wgt(0)), Zm, oh1 * h[0]));
+        q[1] = rfma(R(wgt(1)), bx + cxv, oh1 * h[1]);
+        q[3] = rfma(R(wgt(3)), bx - cxv, oh1 * h[3]);
+        q[2] = rfma(R(wgt(2)), by + cyv, oh1 * h[2]);
+        q[4] = rfma(R(wgt(4)), by - cyv, oh1 * h[4]);
+        q[5] = rfma(R(wgt(5)), (bd + cxy) + (cxv + cyv), oh1 * h[5]);
+        q[7] = rfma(R(wgt(7)), (bd + cxy) - (cxv + cyv), oh1 * h[7]);
+        q[6] = rfma(R(wgt(6)), (bd - cxy) + (cyv - cxv), oh1 * h[6]);
+        q[8] = rfma(R(wgt(8)), (bd - cxy) - (cyv - cxv), oh1 * h[8]);
+        // outflow rows are copied inside push_species; Dirichlet rows get their
+        // incoming populations from the ghost rule below
+        push_species<KIND_H, Pr>(P, pout, N + 1, x, y, q);
         // equilibrium of direction j != 0 (for the ghost rule)
         auto heq = [&](int j) {
-            const double cu = cx(j) * ux + cy(j) * uy;
-            return wgt(j) * fma(Z, fma(4.5 * cu, cu, fma(3.0, cu, -1.5 * uu)), E);
+            const R cu = R(cx(j)) * ux + R(cy(j)) * uy;
+            return R(wgt(j)) * rfma(Z, rfma(R(4.5) * cu, cu, rfma(R(3), cu, R(-1.5) * uu)), E);
         };
         // Dirichlet wall: ghost behind the half-way wall with T_g = 2 T_w - T, u = 0;
         // its post-collision population is h_eq(ghost) + (1 - 1/tau_h)(h_j - h_eq_j).
         if (y == 0 && P.bc[2] == WALL && P.tbc[2] == DIRICHLET) {
-            const double Eg = P.E_ref * (2.0 * P.Tw[2] - T);
-            push_row<2>(P, pout, plane_h(N, 2), x, y, fma(oh1, h[2] - heq(2), wgt(2) * Eg));
-            push_row<5>(P, pout, plane_h(N, 5), x, y, fma(oh1, h[5] - heq(5), wgt(5) * Eg));
-            push_row<6>(P, pout, plane_h(N, 6), x, y, fma(oh1, h[6] - heq(6), wgt(6) * Eg));
-        } else if (y == 0 && P.bc[2] == OUTFLOW) {
-            push_row<2>(P, pout, plane_h(N, 2), x, y, q[2]);
-            push_row<5>(P, pout, plane_h(N, 5), x, y, q[5]);
-            push_row<6>(P, pout, plane_h(N, 6), x, y, q[6]);
+            const R Eg = (R)P.E_ref * (R(2) * (R)P.Tw[2] - T);
+            push_row<2, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[2] - heq(2), R(wgt(2)) * Eg));
+            push_row<5, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[5] - heq(5), R(wgt(5)) * Eg));
+            push_row<6, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[6] - heq(6), R(wgt(6)) * Eg));
         }
         if (y == ny - 1 && P.bc[3] == WALL && P.tbc[3] == DIRICHLET) {
-            const double Eg = P.E_ref * (2.0 * P.Tw[3] - T);
-            push_row<4>(P, pout, plane_h(N, 4), x, y, fma(oh1, h[4] - heq(4), wgt(4) * Eg));
-            push_row<7>(P, pout, plane_h(N, 7), x, y, fma(oh1, h[7] - heq(7), wgt(7) * Eg));
-            push_row<8>(P, pout, plane_h(N, 8), x, y, fma(oh1, h[8] - heq(8), wgt(8) * Eg));
-        } else if (y == ny - 1 && P.bc[3] == OUTFLOW) {
-            push_row<4>(P, pout, plane_h(N, 4), x, y, q[4]);
-            push_row<7>(P, pout, plane_h(N, 7), x, y, q[7]);
-            push_row<8>(P, pout, plane_h(N, 8), x, y, q[8]);
+            const R Eg = (R)P.E_ref * (R(2) * (R)P.Tw[3] - T);
+            push_row<4, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[4] - heq(4), R(wgt(4)) * Eg));
+            push_row<7, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[7] - heq(7), R(wgt(7)) * Eg));
+            push_row<8, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[8] - heq(8), R(wgt(8)) * Eg));
         }
 
         // ---- stage G: lagged planes ------------------------------------------
-        LBM_ST(P, aout, aux_mdot() * S + c, P.aux_elems, 32, mdot);
-        LBM_ST(P, aout, aux_Q() * S + c, P.aux_elems, 33, Zm);
-        LBM_ST(P, aout, aux_psi() * S + c, P.aux_elems, 34, psi);
+        LBM_ST(P, aout, aux_mdot() * S + c, P.aux_elems, 32, (TA)mdot);
+        LBM_ST(P, aout, aux_Q() * S + c, P.aux_elems, 33, (TA)Zm);
+        LBM_ST(P, aout, aux_psi() * S + c, P.aux_elems, 34, (TA)psi);
     }
 }
 

@@ -14,6 +14,8 @@ def test_bytes_per_lu():
     assert bench.bytes_per_lu(2) == 688
     assert bench.bytes_per_lu(3) == 864
     assert bench.bytes_per_lu(4) == 1040
+    assert bench.bytes_per_lu(2, "fp32") == 344
+    assert bench.bytes_per_lu(2, "fp16s") == 216
 
 
 def _free_port():
