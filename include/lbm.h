@@ -176,6 +176,29 @@ int lbm_debug_bounds(lbm_handle* h, long long* out3);
  * shape must be one of the compiled variants (LBM_EINVAL otherwise). */
 int lbm_set_tile(lbm_handle* h, int bx, int by);
 
+/* Diagnostics sums without any allocation, for callers that cannot allocate device
+ * memory when they need them: code that is recording a CUDA graph, a host that owns all
+ * device memory through its own arena, a timed loop that forbids allocation latency.
+ * (The paper has no counterpart: this is a service of the library.)
+ * Inputs are caller-owned device fields of one lattice: phi [N][ny][nx] and the liquid
+ * fraction fl [ny][nx] (as written by lbm_get_fields with LBM_DEVICE); out is a
+ * caller-owned device array of 2N + 2 doubles that receives, as lbm_get_diagnostics does,
+ * sum_x phi_p (N values), sum_x (1 - fl) phi_p (N values), max_x |sum_p phi_p - 1| and the
+ * count of non-finite cells.  The work is queued on `stream` (a cudaStream_t, NULL = the
+ * default stream) and the call returns without synchronising.
+ * The block partial sums live in a fixed array of 608 x 10 doubles (48.6 KiB) in the
+ * library's device image, which every GPU that loads the library holds until the process
+ * exits; any lattice up to 2^31 cells fits in it (a grid-stride loop caps the number of
+ * blocks at 608).  N > LBM_MAXN, a lattice beyond 2^31 cells or a NULL pointer is
+ * rejected with LBM_EINVAL and a message in lbm_last_error(NULL).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the array, so
+ * calls whose work overlaps on the GPU (other streams, other host threads) race; calls
+ * on one stream are ordered and safe.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+int lbm_field_sums_noalloc(const double* phi, const double* fl, int nx, int ny, int N, double* out,
+                           void* stream);
+
 /* Message of the last failing call on h (or of the last failing lbm_create when
  * h is NULL).  Never NULL. */
 const char* lbm_last_error(const lbm_handle* h);
