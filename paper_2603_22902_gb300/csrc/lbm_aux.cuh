@@ -33,7 +33,7 @@ __global__ void init_kernel(const KParams P, const double* __restrict__ phi_in, 
         const double rho = fma(fs, m.rs, fl * m.rl);
         const double cp = fma(fs, m.cs, fl * m.cl);
         const double uu = ux * ux + uy * uy;
-        const double E = P.E_ref * T, Z = rho * cp * T;
+        const double E = P.d.E_ref * T, Z = rho * cp * T;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const double cu = cx(i) * ux + cy(i) * uy;

@@ -76,6 +76,17 @@ static void free_all(lbm_handle* h)
     h->dbg = nullptr;
 }
 
+// FP32 copy of the coefficients, for the policies that compute in FP32.
+static Coef<float> round_coef(const Coef<double>& d)
+{
+    static_assert(sizeof(Coef<double>) == 2 * sizeof(Coef<float>), "Coef holds only T members");
+    Coef<float> f{};
+    const double* src = reinterpret_cast<const double*>(&d);
+    float* dst = reinterpret_cast<float*>(&f);
+    for (size_t k = 0; k < sizeof(Coef<double>) / sizeof(double); ++k) dst[k] = (float)src[k];
+    return f;
+}
+
 extern "C" {
 
 int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_thermal* th, const lbm_bc* bc,
@@ -141,49 +152,50 @@ int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_t
     for (int s = 0; s < 4; ++s) {
         P.bc[s] = bc->kind[s];
         P.tbc[s] = bc->tkind[s];
-        P.Tw[s] = bc->T_wall[s];
+        P.d.Tw[s] = bc->T_wall[s];
     }
     for (int p = 0; p < N; ++p) {
         const lbm_phase& ph = phases[p];
-        P.rho_l[p] = ph.rho_l;
-        P.rho_s[p] = ph.rho_s;
-        P.mu_l[p] = ph.mu_l;
-        P.mu_s[p] = ph.mu_s;
-        P.lam_l[p] = ph.lambda_l;
-        P.lam_s[p] = ph.lambda_s;
-        P.cp_l[p] = ph.cp_l;
-        P.cp_s[p] = ph.cp_s;
+        P.d.rho_l[p] = ph.rho_l;
+        P.d.rho_s[p] = ph.rho_s;
+        P.d.mu_l[p] = ph.mu_l;
+        P.d.mu_s[p] = ph.mu_s;
+        P.d.lam_l[p] = ph.lambda_l;
+        P.d.lam_s[p] = ph.lambda_s;
+        P.d.cp_l[p] = ph.cp_l;
+        P.d.cp_s[p] = ph.cp_s;
         P.rhoL[p] = ph.rho_l * ph.latent;
-        P.drho[p] = ph.rho_s - ph.rho_l;
-        P.pcm[p] = ph.latent > 0.0 ? 1.0 : 0.0;
+        P.d.drho[p] = ph.rho_s - ph.rho_l;
+        P.d.pcm[p] = ph.latent > 0.0 ? 1.0 : 0.0;
         for (int q = 0; q < N; ++q) {
             const double sig = num->sigma[p * LBM_MAXN + q];
-            P.b2[p][q] = 2.0 * 3.0 / num->eps * sig;      // 2 beta_pq
-            P.kk[p][q] = 3.0 * num->eps / 4.0 * sig;      // -k_pq
+            P.d.b2[p][q] = 2.0 * 3.0 / num->eps * sig;      // 2 beta_pq
+            P.d.kk[p][q] = 3.0 * num->eps / 4.0 * sig;      // -k_pq
             for (int s = 0; s < 4; ++s)
-                P.wet[s][p][q] = bc->kind[s] == LBM_BC_WALL ? 4.0 / num->eps * bc->wet_cos[s][p * LBM_MAXN + q] : 0.0;
+                P.d.wet[s][p][q] = bc->kind[s] == LBM_BC_WALL ? 4.0 / num->eps * bc->wet_cos[s][p * LBM_MAXN + q] : 0.0;
         }
     }
-    P.four_eps = 4.0 / num->eps;
+    P.d.four_eps = 4.0 / num->eps;
     P.T_sol = th->T_sol;
     P.T_liq = th->T_liq;
     const double cp_ref = th->cp_ref > 0.0 ? th->cp_ref
                                            : 2.0 * phases[0].cp_s * phases[0].cp_l / (phases[0].cp_s + phases[0].cp_l);
-    P.E_ref = th->rho_ref * cp_ref;
-    P.tau_h_scale = 3.0 / P.E_ref;
-    P.us[0] = th->u_solid[0];
-    P.us[1] = th->u_solid[1];
-    P.accel[0] = th->accel[0];
-    P.accel[1] = th->accel[1];
+    P.d.E_ref = th->rho_ref * cp_ref;
+    P.d.tau_h_scale = 3.0 / P.d.E_ref;
+    P.d.us[0] = th->u_solid[0];
+    P.d.us[1] = th->u_solid[1];
+    P.d.accel[0] = th->accel[0];
+    P.d.accel[1] = th->accel[1];
     const double tau_g = num->mobility * 3.0 + 0.5;
-    P.omega_g = 1.0 / tau_g;
-    P.kg = 1.0 - 0.5 * P.omega_g;
+    P.d.omega_g = 1.0 / tau_g;
+    P.d.kg = 1.0 - 0.5 * P.d.omega_g;
 
     const size_t pb = plane_bytes(h);
     P.rest_elems = (long long)(N + 2) * P.S;
     P.move_elems = 8LL * (N + 2) * P.S;
     P.aux_elems = (long long)naux_planes(N) * P.S;
-    P.inv_E_ref = 1.0 / P.E_ref;
+    P.d.inv_E_ref = 1.0 / P.d.E_ref;
+    P.f = round_coef(P.d);
     P.dbg = nullptr;
     dispatch(N, h->precision, [&](auto n, auto pr) {
         using Pr = decltype(pr);

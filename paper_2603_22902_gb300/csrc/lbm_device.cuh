@@ -16,33 +16,55 @@ __host__ __device__ constexpr int cy(int i) { return i == 2 || i == 5 || i == 6 
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i < 5 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5); }
 __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
 
+// Arithmetic helpers for the compute type R of a precision policy.
+__device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double rrsqrt(double a) { return rsqrt(a); }
+__device__ __forceinline__ float rrsqrt(float a) { return rsqrtf(a); }
+
+// Per-run coefficients used by the arithmetic of the step, in type T.  The host fills
+// a double and a float copy, so a policy computing in FP32 reads float constants and
+// converts nothing per cell (FP64 <-> FP32 conversions share the FP64 unit).
+template <class T>
+struct Coef {
+    // eq. 2 mixture coefficients per phase
+    T rho_l[MAXN], rho_s[MAXN], mu_l[MAXN], mu_s[MAXN];
+    T lam_l[MAXN], lam_s[MAXN], cp_l[MAXN], cp_s[MAXN];
+    T drho[MAXN];                 // rho_s^p - rho_l^p
+    T pcm[MAXN];                  // 1 where L_p > 0 (the phase changes phase), else 0
+    // Section 2 free energy: 2 beta_pq = 6 sigma_pq / eps and -k_pq = 3 eps sigma_pq / 4
+    T b2[MAXN][MAXN], kk[MAXN][MAXN];
+    T four_eps;                   // 4 / eps
+    T wet[4][MAXN][MAXN];         // (4 / eps) cos(theta_pq) per wall side (0 elsewhere)
+    T E_ref;                      // rho_ref c_p,ref
+    T inv_E_ref;                  // 1 / (rho_ref c_p,ref)
+    T tau_h_scale;                // 1 / (rho_ref c_p,ref c_s^2)
+    T us[2], accel[2];
+    T omega_g, kg;                // 1 / tau_g and 1 - 1/(2 tau_g), tau_g = M / c_s^2 + 1/2
+    T Tw[4];                      // Dirichlet wall temperature
+};
+
 // Parameter block passed by value to every kernel (lives in the constant bank).
 // Everything derivable once per run is derived on the host.
 struct KParams {
     int nx, ny, N;
     long long S;                  // plane stride in elements (nx * ny)
     int bc[4], tbc[4];            // side kinds, sides 0 x-min, 1 x-max, 2 y-min, 3 y-max
-    double Tw[4];                 // Dirichlet wall temperature
-    // eq. 2 mixture coefficients per phase
-    double rho_l[MAXN], rho_s[MAXN], mu_l[MAXN], mu_s[MAXN];
-    double lam_l[MAXN], lam_s[MAXN], cp_l[MAXN], cp_s[MAXN];
+    Coef<double> d;               // coefficients, FP64
+    Coef<float> f;                // the same, rounded to FP32
     double rhoL[MAXN];            // rho_l^p L_p: latent heat per volume of pure phase p
-    double drho[MAXN];            // rho_s^p - rho_l^p
-    double pcm[MAXN];             // 1 where L_p > 0 (the phase changes phase), else 0
-    // Section 2 free energy: 2 beta_pq = 6 sigma_pq / eps and -k_pq = 3 eps sigma_pq / 4
-    double b2[MAXN][MAXN], kk[MAXN][MAXN];
-    double four_eps;              // 4 / eps
-    double wet[4][MAXN][MAXN];    // (4 / eps) cos(theta_pq) per wall side (0 elsewhere)
     double T_sol, T_liq;
-    double E_ref;                 // rho_ref c_p,ref
-    double tau_h_scale;           // 1 / (rho_ref c_p,ref c_s^2)
-    double us[2], accel[2];
-    double omega_g, kg;           // 1 / tau_g and 1 - 1/(2 tau_g), tau_g = M / c_s^2 + 1/2
     long long rest_elems, move_elems; // elements of the rest / moving block of one population set
     long long aux_elems;          // elements of one lagged set
-    double inv_E_ref;             // 1 / (rho_ref c_p,ref)
     unsigned long long* dbg;      // LBM_CHECK_BOUNDS builds: {violations, first site, first index}
 };
+
+template <class R>
+__device__ __forceinline__ const Coef<R>& coef(const KParams& P)
+{
+    if constexpr (sizeof(R) == sizeof(double)) return P.d;
+    else return P.f;
+}
 
 // Global-memory access with an optional bounds check.  In LBM_CHECK_BOUNDS builds an
 // out-of-range index is recorded in P.dbg (count, site code, index) and the access is
@@ -86,7 +108,7 @@ __host__ __device__ constexpr int aux_phiux(int p) { return 3 + p; }
 __host__ __device__ constexpr int aux_phiuy(int N, int p) { return 3 + N + p; }
 __host__ __device__ constexpr int naux_planes(int N) { return 3 + 2 * N; }
 
-// Mixture (eq. 2) sums over the phases.
+// Mixture (eq. 2) sums over the phases, FP64 (initial state and the map).
 template <int N>
 struct Mix {
     double rs, rl, cs, cl, Lv, dr, pcm;
@@ -98,15 +120,41 @@ __device__ __forceinline__ Mix<N> mixture_core(const KParams& P, const double (&
     Mix<N> m{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int p = 0; p < N; ++p) {
-        m.rs = fma(phi[p], P.rho_s[p], m.rs);
-        m.rl = fma(phi[p], P.rho_l[p], m.rl);
-        m.cs = fma(phi[p], P.cp_s[p], m.cs);
-        m.cl = fma(phi[p], P.cp_l[p], m.cl);
+        m.rs = fma(phi[p], P.d.rho_s[p], m.rs);
+        m.rl = fma(phi[p], P.d.rho_l[p], m.rl);
+        m.cs = fma(phi[p], P.d.cp_s[p], m.cs);
+        m.cl = fma(phi[p], P.d.cp_l[p], m.cl);
         m.Lv = fma(phi[p], P.rhoL[p], m.Lv);
-        m.dr = fma(phi[p], P.drho[p], m.dr);
-        m.pcm = fma(phi[p], P.pcm[p], m.pcm);
+        m.dr = fma(phi[p], P.d.drho[p], m.dr);
+        m.pcm = fma(phi[p], P.d.pcm[p], m.pcm);
     }
     return m;
+}
+
+// The part of the mixture that eq. H needs (FP64 in every precision): rs, rl, cs, cl, Lv.
+template <int N>
+__device__ __forceinline__ Mix<N> mixture_map(const KParams& P, const double (&phi)[N])
+{
+    Mix<N> m{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        m.rs = fma(phi[p], P.d.rho_s[p], m.rs);
+        m.rl = fma(phi[p], P.d.rho_l[p], m.rl);
+        m.cs = fma(phi[p], P.d.cp_s[p], m.cs);
+        m.cl = fma(phi[p], P.d.cp_l[p], m.cl);
+        m.Lv = fma(phi[p], P.rhoL[p], m.Lv);
+    }
+    return m;
+}
+
+// sum_p phi_p a_p in the arithmetic type R (same order of operations as mixture_core).
+template <int N, class R>
+__device__ __forceinline__ R mix_sum(const R (&phi)[N], const R (&a)[MAXN])
+{
+    R v = R(0);
+#pragma unroll
+    for (int p = 0; p < N; ++p) v = rfma(phi[p], a[p], v);
+    return v;
 }
 
 // eq. H: liquid fraction (and, with WANT_T, temperature) from rho H.

@@ -44,6 +44,7 @@ struct PrecFP64 {
     static constexpr bool QUANT = false;
     static constexpr double NABS2 = 1e-24;
     static constexpr float NGUARD = 0.0f;
+    static constexpr int OCC_THREADS = 512;
 };
 struct PrecFP32 {
     using R = float;
@@ -53,6 +54,7 @@ struct PrecFP32 {
     static constexpr bool QUANT = false;
     static constexpr double NABS2 = 1e-10;
     static constexpr float NGUARD = 1e-3f;
+    static constexpr int OCC_THREADS = 768;
 };
 struct PrecFP16S {
     using R = float;
@@ -62,6 +64,7 @@ struct PrecFP16S {
     static constexpr bool QUANT = true;
     static constexpr double NABS2 = 1e-6;
     static constexpr float NGUARD = 3e-2f;
+    static constexpr int OCC_THREADS = 768;
 };
 struct PrecBF16S {
     using R = float;
@@ -71,6 +74,7 @@ struct PrecBF16S {
     static constexpr bool QUANT = true;
     static constexpr double NABS2 = 1e-6;
     static constexpr float NGUARD = 3e-2f;
+    static constexpr int OCC_THREADS = 768;
 };
 
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
@@ -81,12 +85,6 @@ template <class T> __device__ __forceinline__ T from_f(float v);
 template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
-
-// Arithmetic helpers for the compute type R.
-__device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double rrsqrt(double a) { return rsqrt(a); }
-__device__ __forceinline__ float rrsqrt(float a) { return rsqrtf(a); }
 
 // Byte sizes of one population set and one lagged set.
 template <class Pr>

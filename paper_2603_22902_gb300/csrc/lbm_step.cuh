@@ -71,7 +71,7 @@ __device__ __forceinline__ typename Pr::R ld_pop(const KParams& P, const PopView
         const float qf = to_f(q);
         if (KIND == KIND_F) return qf * (w * F_SCALE);
         if (KIND == KIND_G) return qf * w;
-        return qf * (w * (float)P.E_ref);
+        return qf * (w * P.f.E_ref);
     }
 }
 
@@ -93,7 +93,7 @@ __device__ __forceinline__ void st_pop(const KParams& P, const PopView<Pr>& v, i
         float q;
         if (KIND == KIND_F) q = (float)val * (1.0f / (w * F_SCALE));
         else if (KIND == KIND_G) q = (float)val * (1.0f / w);
-        else q = (float)val * (1.0f / w) * (float)P.inv_E_ref;
+        else q = (float)val * (1.0f / w) * P.f.inv_E_ref;
         LBM_ST(P, v.move, idx, P.move_elems, site, from_f<TM>(q));
     }
 }
@@ -108,26 +108,28 @@ __device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>
     const long long S = P.S;
     const R mdm = (R)LBM_LD(P, ain, aux_mdot() * S + c, P.aux_elems, 1);
     const R Qm = (R)LBM_LD(P, ain, aux_Q() * S + c, P.aux_elems, 2);
-    const R den = R(1) - R(0.5) * mdm;
+    const R iden = R(1) / (R(1) - R(0.5) * mdm);
     double phd[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) {
         R s = R(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) s += ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 3);
-        phi[p] = s / den;
+        phi[p] = s * iden;
         phd[p] = (double)phi[p];
     }
     R sh = R(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 4);
     const double rhoH = (double)rfma(R(0.5), Qm, sh);
-    const Mix<N> m = mixture_core<N>(P, phd);
-    double fl, T;
-    enthalpy_map<N, false>(P, m, rhoH, fl, T);
-    const double fs = 1.0 - fl;
-    rho = (R)fma(fs, m.rs, fl * m.rl);
-    psi = (R)(fs * m.dr);
+    // eq. H in FP64; the rest of eq. 2 in R
+    const Mix<N> m = mixture_map<N>(P, phd);
+    double fld, T;
+    enthalpy_map<N, false>(P, m, rhoH, fld, T);
+    const Coef<R>& C = coef<R>(P);
+    const R fl = (R)fld, fs = R(1) - fl;
+    rho = rfma(fs, mix_sum<N, R>(phi, C.rho_s), fl * mix_sum<N, R>(phi, C.rho_l));
+    psi = fs * mix_sum<N, R>(phi, C.drho);
 }
 
 // Push one post-collision population q_j of species s at node (x, y) into set B.
@@ -200,8 +202,15 @@ __device__ __forceinline__ void push_species(const KParams& P, const PopView<Pr>
     }
 }
 
+// Resident threads per SM the register allocation must allow (launch bounds): the
+// policy's choice, or LBM_OCC_THREADS when a build overrides it for tuning.
+#ifdef LBM_OCC_THREADS
+#define LBM_OCC(Pr) (LBM_OCC_THREADS)
+#else
+#define LBM_OCC(Pr) (Pr::OCC_THREADS)
+#endif
 template <int N, int TX, int TY, bool COLLIDE, class Pr>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(TX * TY, (LBM_OCC(Pr) + TX * TY - 1) / (TX * TY))
 fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __restrict__ pout_base,
                   const typename Pr::TA* __restrict__ ain, typename Pr::TA* __restrict__ aout, ExportPtrs ex)
 {
@@ -221,6 +230,7 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
     const bool owned = x < nx && y < ny;
     const bool xper = P.bc[0] == PERIODIC, yper = P.bc[2] == PERIODIC;
     const PopView<Pr> pin = pop_view<Pr>(P, pin_base);
+    const Coef<R>& C = coef<R>(P);
 
     // The cell coordinates are brought into range before anything else (periodic:
     // full modulo, since a tile may be wider / taller than the domain; otherwise:
@@ -264,41 +274,33 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
         for (int i = 0; i < 9; ++i) h[i] = ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 7);
         const R mdm = (R)LBM_LD(P, ain, aux_mdot() * S + c, P.aux_elems, 8);
         const R Qm = (R)LBM_LD(P, ain, aux_Q() * S + c, P.aux_elems, 9);
-        const R den = R(1) - R(0.5) * mdm;
+        const R iden = R(1) / (R(1) - R(0.5) * mdm);
         double phd[N];
 #pragma unroll
         for (int p = 0; p < N; ++p) {
             R s = R(0);
 #pragma unroll
             for (int i = 0; i < 9; ++i) s += g[p][i];
-            phi[p] = s / den;
+            phi[p] = s * iden;
             phd[p] = (double)phi[p];
         }
         R sh = R(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) sh += h[i];
         rhoH = rfma(R(0.5), Qm, sh);
-        // eq. 2 + eq. H in FP64
-        const Mix<N> m = mixture_core<N>(P, phd);
+        // eq. H in FP64, the rest of eq. 2 in R
+        const Mix<N> m = mixture_map<N>(P, phd);
         double fld, Td;
         enthalpy_map<N, true>(P, m, (double)rhoH, fld, Td);
-        const double fs = 1.0 - fld;
-        double ms = 0.0, ml = 0.0, ks = 0.0, kl = 0.0;
-#pragma unroll
-        for (int p = 0; p < N; ++p) {
-            ms = fma(phd[p], P.mu_s[p], ms);
-            ml = fma(phd[p], P.mu_l[p], ml);
-            ks = fma(phd[p], P.lam_s[p], ks);
-            kl = fma(phd[p], P.lam_l[p], kl);
-        }
         fl = (R)fld;
         T = (R)Td;
-        rho = (R)fma(fs, m.rs, fld * m.rl);
-        mu = (R)fma(fs, ms, fld * ml);
-        lam = (R)fma(fs, ks, fld * kl);
-        cp = (R)fma(fs, m.cs, fld * m.cl);
-        psi = (R)(fs * m.dr);
-        chi = (R)(fs * m.pcm);
+        const R fs = R(1) - fl;
+        rho = rfma(fs, mix_sum<N, R>(phi, C.rho_s), fl * mix_sum<N, R>(phi, C.rho_l));
+        mu = rfma(fs, mix_sum<N, R>(phi, C.mu_s), fl * mix_sum<N, R>(phi, C.mu_l));
+        lam = rfma(fs, mix_sum<N, R>(phi, C.lam_s), fl * mix_sum<N, R>(phi, C.lam_l));
+        cp = rfma(fs, mix_sum<N, R>(phi, C.cp_s), fl * mix_sum<N, R>(phi, C.cp_l));
+        psi = fs * mix_sum<N, R>(phi, C.drho);
+        chi = fs * mix_sum<N, R>(phi, C.pcm);
 #pragma unroll
         for (int p = 0; p < N; ++p) s_phi[p][ty + 1][tx + 1] = phi[p];
         s_rho[ty + 1][tx + 1] = rho;
@@ -336,10 +338,10 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
 #pragma unroll
             for (int q = 0; q < N; ++q) {
                 if (q == p) continue;
-                double cw = 0.0;
-                if (wx >= 0) cw += P.wet[wx][p][q];
-                if (wy >= 0) cw += P.wet[wy][p][q];
-                corr = rfma((R)cw * ph[p], ph[q], corr);
+                R cw = R(0);
+                if (wx >= 0) cw += C.wet[wx][p][q];
+                if (wy >= 0) cw += C.wet[wy][p][q];
+                corr = rfma(cw * ph[p], ph[q], corr);
             }
             s_phi[p][ly][lx] = ph[p] + corr;
         }
@@ -387,14 +389,17 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
             const R s = phi[p] + phi[q];
             R nxv = R(0), nyv = R(0);
             if (s > R(1e-12)) {
-                const R is2 = R(1) / (s * s);
-                const R Gx = (phi[q] * gpx[p] - phi[p] * gpx[q]) * is2;
-                const R Gy = (phi[q] * gpy[p] - phi[p] * gpy[q]) * is2;
+                // n_pq = grad(phi_p / s) / |grad(phi_p / s)|, s = phi_p + phi_q; the quotient
+                // rule gives grad(phi_p / s) = G / s^2 with G below, so n_pq = G / |G| and the
+                // guard |grad(phi_p / s)| > threshold reads |G|^2 > threshold^2 s^4
+                const R Gx = phi[q] * gpx[p] - phi[p] * gpx[q];
+                const R Gy = phi[q] * gpy[p] - phi[p] * gpy[q];
                 const R G2 = Gx * Gx + Gy * Gy;
-                bool ok = G2 > R(Pr::NABS2);
+                const R s2 = s * s;
+                bool ok = G2 > R(Pr::NABS2) * (s2 * s2);
                 if constexpr (Pr::NGUARD > 0.0f) {
-                    const R ref = (phi[q] * phi[q] * (gpx[p] * gpx[p] + gpy[p] * gpy[p]) +
-                                   phi[p] * phi[p] * (gpx[q] * gpx[q] + gpy[q] * gpy[q])) * (is2 * is2);
+                    const R ref = phi[q] * phi[q] * (gpx[p] * gpx[p] + gpy[p] * gpy[p]) +
+                                  phi[p] * phi[p] * (gpx[q] * gpx[q] + gpy[q] * gpy[q]);
                     ok = ok && G2 > R(Pr::NGUARD * Pr::NGUARD) * ref;
                 }
                 if (ok) {
@@ -403,16 +408,16 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
                     nyv = Gy * r;
                 }
             }
-            const R a = (R)P.four_eps * phi[p] * phi[q];
+            const R a = C.four_eps * phi[p] * phi[q];
             Rx[p] = rfma(a, nxv, Rx[p]);
             Ry[p] = rfma(a, nyv, Ry[p]);
             Rx[q] = rfma(-a, nxv, Rx[q]);
             Ry[q] = rfma(-a, nyv, Ry[q]);
             const R gs = R(2) * s * (R(1) - s) * (R(1) - R(2) * s);
-            mup[p] += rfma((R)P.b2[p][q], gpv[p] - gs, (R)P.kk[p][q] * lap[q]);
-            mup[q] += rfma((R)P.b2[q][p], gpv[q] - gs, (R)P.kk[q][p] * lap[p]);
+            mup[p] += rfma(C.b2[p][q], gpv[p] - gs, C.kk[p][q] * lap[q]);
+            mup[q] += rfma(C.b2[q][p], gpv[q] - gs, C.kk[q][p] * lap[p]);
         }
-    R Fx = rho * (R)P.accel[0], Fy = rho * (R)P.accel[1];
+    R Fx = rho * C.accel[0], Fy = rho * C.accel[1];
 #pragma unroll
     for (int p = 0; p < N; ++p) {
         Fx = rfma(mup[p], gpx[p], Fx);
@@ -423,9 +428,17 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
     const R jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
     const R jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
     const R sum_f = ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
-    const R irho = R(1) / rho;
+    // 1 / rho, omega_f = 1 / tau_f = rho / A and omega_h = 1 / tau_h = 1 / B from one
+    // division: tau_f = A / rho, A = 3 mu + rho / 2 (tau_f = mu / (rho c_s^2) + 1/2) and
+    // tau_h = B = lambda / (rho_ref c_p,ref c_s^2) + 1/2
+    const R Af = rfma(R(3), mu, R(0.5) * rho);
+    const R Bh = rfma(lam, C.tau_h_scale, R(0.5));
+    const R rAB = R(1) / (rho * Af * Bh);
+    const R irho = (Af * Bh) * rAB;
+    const R om = (rho * rho) * (Bh * rAB);
+    const R oh = (rho * Af) * rAB;
     const R usx = rfma(R(0.5), Fx, jx) * irho, usy = rfma(R(0.5), Fy, jy) * irho;
-    const R fpx = chi * ((R)P.us[0] - usx), fpy = chi * ((R)P.us[1] - usy);
+    const R fpx = chi * (C.us[0] - usx), fpy = chi * (C.us[1] - usy);
     const R ux = rfma(R(0.5), fpx, usx), uy = rfma(R(0.5), fpy, usy);
     const R psim = (R)LBM_LD(P, ain, aux_psi() * S + c, P.aux_elems, 14);
     const R mdot = -((psi - psim) + (ux * gsx + uy * gsy)) * irho;
@@ -433,10 +446,10 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
     const R Lxx = rfma(R(2) * ux, Fx, Ssrc * R(1.0 / 3.0));
     const R Lyy = rfma(R(2) * uy, Fy, Ssrc * R(1.0 / 3.0));
     const R Lxy = rfma(ux, Fy, uy * Fx);
-    const R tau_f = rfma(R(3) * mu, irho, R(0.5));
+    const R tmh = R(3) * mu * irho;  // tau_f - 1/2
     const R F0 = R(wgt(0)) * rfma(R(-1.5), Lxx + Lyy, Ssrc);
     const R uu = rfma(ux, ux, uy * uy);
-    const R p = R(0.6) * (((sum_f + R(0.5) * Ssrc) + (tau_f - R(0.5)) * F0) - rho * R(wgt(0)) * R(1.5) * uu);
+    const R p = R(0.6) * (((sum_f + R(0.5) * Ssrc) + tmh * F0) - rho * R(wgt(0)) * R(1.5) * uu);
 
     if (!COLLIDE) {
 #pragma unroll
@@ -454,7 +467,7 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
 
     // ---- stage F: flow collision -------------------------------------------
     {
-        const R om = R(1) / tau_f, k = rfma(R(-0.5), om, R(1)), om1 = R(1) - om;
+        const R k = rfma(R(-0.5), om, R(1)), om1 = R(1) - om;
         const R Fex = rfma(rho, fpx, Fx), Fey = rfma(rho, fpy, Fy);
         const R rom = om * rho;
         const R a0 = om * rfma(R(-1.5) * rho, uu, R(3) * p) + k * rfma(R(-1.5), Lxx + Lyy, Ssrc);
@@ -482,7 +495,7 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
 
     // ---- stage F: phase-field collisions -------------------------------------
     {
-        const R og = (R)P.omega_g, kg = (R)P.kg, og1 = R(1) - og;
+        const R og = C.omega_g, kg = C.kg, og1 = R(1) - og;
 #pragma unroll
         for (int pp = 0; pp < N; ++pp) {
             const R Dx = phi[pp] * ux - (R)LBM_LD(P, ain, aux_phiux(pp) * S + c, P.aux_elems, 15);
@@ -508,8 +521,8 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
 
     // ---- stage F: enthalpy collision + Dirichlet ghosts ---------------------
     {
-        const R Z = rho * cp * T, E = (R)P.E_ref * T;
-        const R oh = R(1) / rfma(lam, (R)P.tau_h_scale, R(0.5)), kh = rfma(R(-0.5), oh, R(1)), oh1 = R(1) - oh;
+        const R Z = rho * cp * T, E = C.E_ref * T;
+        const R kh = rfma(R(-0.5), oh, R(1)), oh1 = R(1) - oh;
         const R Zm = Z * mdot;
         const R c0 = oh * rfma(R(-1.5) * Z, uu, E) + kh * Zm;
         const R ohZ = oh * Z;
@@ -538,13 +551,13 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
         // Dirichlet wall: ghost behind the half-way wall with T_g = 2 T_w - T, u = 0;
         // its post-collision population is h_eq(ghost) + (1 - 1/tau_h)(h_j - h_eq_j).
         if (y == 0 && P.bc[2] == WALL && P.tbc[2] == DIRICHLET) {
-            const R Eg = (R)P.E_ref * (R(2) * (R)P.Tw[2] - T);
+            const R Eg = C.E_ref * (R(2) * C.Tw[2] - T);
             push_row<2, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[2] - heq(2), R(wgt(2)) * Eg));
             push_row<5, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[5] - heq(5), R(wgt(5)) * Eg));
             push_row<6, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[6] - heq(6), R(wgt(6)) * Eg));
         }
         if (y == ny - 1 && P.bc[3] == WALL && P.tbc[3] == DIRICHLET) {
-            const R Eg = (R)P.E_ref * (R(2) * (R)P.Tw[3] - T);
+            const R Eg = C.E_ref * (R(2) * C.Tw[3] - T);
             push_row<4, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[4] - heq(4), R(wgt(4)) * Eg));
             push_row<7, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[7] - heq(7), R(wgt(7)) * Eg));
             push_row<8, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[8] - heq(8), R(wgt(8)) * Eg));

