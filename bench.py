@@ -12,6 +12,11 @@ a barrier + device synchronise; the max over ranks is reported.  With N > 1 ever
 runs its own replica of the workload (replicas only: the single-lattice step has no
 multi-GPU path here), so the scaling is weak.
 
+With --precision fp64 (the default) and one GPU, the line also carries
+"reduced_precision": the --compare policy (FP16 storage by default) timed the same way
+on the same workload, and the freezing-front position of both after --front-steps steps
+from the same initial state (the error bound is 0.5 lattice units).
+
 The reference arm (--impl reference) times the CPU oracle (oracle/) as it stands on
 the host cores, one oracle time step of the same workload per step.
 """
@@ -43,11 +48,21 @@ def bytes_per_lu(N: int, precision: str = "fp64") -> int:
     return 2 * ((N + 2) * er + 8 * (N + 2) * em + (3 + 2 * N) * ea)
 
 
-# FP64 operations per lattice update of the fused step kernel (collision path), counted
-# from the SASS instruction mix with ncu (DFMA = 2, DADD/DMUL = 1); see the profile notes.
-FP64_FLOP_PER_LU = {2: None, 3: None, 4: None}
-# FP64 peak of a GB300 from unit counts: 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# The FP64 step is bound by the FP64 pipe, not by HBM.  Its roofline is the issue rate
+# of that pipe: 152 SMs x 2 FP64 lanes per clock x 2.07 GHz = 629.3 G thread-instructions
+# per second (x 2 flop per FMA = 1.259 TFLOP/s).
+FP64_PIPE_PEAK_GINST = 152 * 2 * 2.070
+# Per lattice update of the fused step kernel, from one ncu capture of the kernel built
+# from the sources with digest `digest` (sessile drop 512^2, N = 2, 32 x 8 tiles):
+# FP64-pipe thread-instructions, FP64 flop (DFMA = 2, DADD / DMUL = 1) and DRAM bytes.
+# A changed kernel has another digest, and then these counts are not reported.
+# (DRAM bytes are what ncu saw during the launch: part of the writes of a launch is
+# still in L2 when it ends and reaches DRAM during the next one.)
+_D = "d84fc5df574b01a655f96165177cd35a00cb130c88640a63d2c84f6ec302c7d3"
+NCU_COUNTS = {
+    ("fp64", 2): {"digest": _D, "fp64_inst": 491.6, "fp64_flop": 666.7, "dram_bytes": 507.9},
+    ("fp16s", 2): {"digest": _D, "fp64_inst": 36.5, "fp64_flop": 50.1, "dram_bytes": 108.5},
+}
 
 
 def load_peaks():
@@ -57,6 +72,18 @@ def load_peaks():
             d = json.load(fh)
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def kernel_digest():
+    from paper_2603_22902_gb300 import build as B
+    return B._sources_digest()
+
+
+def ncu_counts(precision, N):
+    c = NCU_COUNTS.get((precision, N))
+    if c and c["digest"] == kernel_digest():
+        return c
+    return None
 
 
 def make_case(name):
@@ -239,20 +266,20 @@ def run_gpu(args):
     hbm_peak, peak_kind = load_peaks()
     bpl = bytes_per_lu(N, args.precision)
     gbs = bpl * mlups_rank * 1e6 / 1e9
+    counts = ncu_counts(args.precision, N)
+    traffic = round(counts["dram_bytes"] * cells) if counts else None
     roof_hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(gbs / hbm_peak, 4), "traffic": args.traffic,
-                "peak_kind": peak_kind, "bytes_per_lu": bpl}
+                "frac": round(gbs / hbm_peak, 4), "traffic": traffic,
+                "peak_kind": f"{peak_kind} (copy bandwidth)", "bytes_per_lu": bpl, "lu_per_launch": cells}
     roofline = roof_hbm
-    flop = FP64_FLOP_PER_LU.get(N) if args.precision == "fp64" else None
-    alu = None
-    if flop:
-        tf = flop * mlups_rank * 1e6 / 1e12
-        alu = {"bound": "alu", "achieved": round(tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-               "frac": round(tf / FP64_PEAK_TFLOPS, 4), "traffic": args.traffic, "flop_per_lu": flop,
-               "peak_kind": "derived from unit counts and max clock"}
-        if alu["frac"] > roof_hbm["frac"]:
-            roofline = dict(alu)
-            roofline["hbm"] = {k: roof_hbm[k] for k in ("achieved", "peak", "unit", "frac")}
+    if counts and args.precision == "fp64":
+        gi = counts["fp64_inst"] * mlups_rank * 1e6 / 1e9
+        roofline = {"bound": "alu", "achieved": round(gi, 1), "peak": round(FP64_PIPE_PEAK_GINST, 1),
+                    "unit": "G FP64-pipe inst/s", "frac": round(gi / FP64_PIPE_PEAK_GINST, 4), "traffic": traffic,
+                    "peak_kind": "derived: 152 SMs x 2 FP64 lanes/clock x 2.07 GHz",
+                    "fp64_inst_per_lu": counts["fp64_inst"], "lu_per_launch": cells,
+                    "tflops": round(counts["fp64_flop"] * mlups_rank * 1e6 / 1e12, 4),
+                    "hbm": {k: roof_hbm[k] for k in ("achieved", "peak", "unit", "frac", "bytes_per_lu")}}
 
     # ---- end to end through the C ABI with host buffers ------------------------------
     e2e = None
@@ -282,6 +309,9 @@ def run_gpu(args):
                "sample": f"{done} oracle time steps of {case.name} ({dt:.1f} s), one host thread"}
 
     s.close()
+    rp = None
+    if world == 1 and args.precision == "fp64" and args.compare and args.compare != "none":
+        rp = compare_precision(case, args.compare, mlups_rank, args.front_steps, stream, flush)
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
@@ -295,8 +325,8 @@ def run_gpu(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clk, "wall_s_timed_loop": round(t_wall, 4),
         }
-        if alu is not None and roofline is roof_hbm:
-            line["roofline_alu"] = alu
+        if rp is not None:
+            line["reduced_precision"] = rp
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -304,17 +334,57 @@ def run_gpu(args):
     return 0
 
 
+def timed_mlups(lbm, case, precision, steps, stream, flush):
+    """Same protocol as the headline: L2 flushed before every timed step, CUDA events."""
+    import torch
+    s = lbm.Solver(case, precision=precision).set_fields()
+    s.step(5)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        s.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    s.close()
+    t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    return case.cells * steps / (t_ms * 1e-3) / 1e6
+
+
+def compare_precision(case, precision, mlups_fp64, front_steps, stream, flush):
+    """Reduced-precision storage against FP64 on the same GPU: throughput, and the
+    freezing-front position after front_steps steps from the same initial state."""
+    from paper_2603_22902_gb300 import lbm
+    from paper_2603_22902_gb300.metrics import front_height
+    mlups = timed_mlups(lbm, case, precision, 300, stream, flush)
+    out = {"precision": precision, "value": round(mlups, 2), "unit": "MLUPS",
+           "speedup_vs_fp64": round(mlups / mlups_fp64, 3), "bytes_per_lu": bytes_per_lu(case.N, precision)}
+    if front_steps > 0:
+        fr = {}
+        for prec in ("fp64", precision):
+            s = lbm.Solver(case, precision=prec).set_fields()
+            s.step(front_steps)
+            fr[prec] = front_height(s.fields_numpy(), case.nx)
+            s.close()
+        out.update({"front_steps": front_steps, "front_fp64_lu": round(fr["fp64"], 4),
+                    "front_err_lu": round(abs(fr[precision] - fr["fp64"]), 4), "front_err_bound_lu": 0.5})
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sessile_drop_512")
     ap.add_argument("--precision", default="fp64")
     ap.add_argument("--tile", type=int, nargs=2, default=None)
     ap.add_argument("--e2e-steps", type=int, default=100)
-    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch, if measured")
+    ap.add_argument("--compare", default="fp16s", help="reduced precision timed beside fp64 ('none' to skip)")
+    ap.add_argument("--front-steps", type=int, default=15000)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

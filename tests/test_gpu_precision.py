@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from paper_2603_22902_gb300 import workloads as W
+from paper_2603_22902_gb300.metrics import front_height
 
 pytestmark = pytest.mark.gpu
 
@@ -35,11 +36,6 @@ def lbm():
     B.build()
     from paper_2603_22902_gb300 import lbm as L
     return L
-
-
-def front_height(F, nx):
-    cols = slice(nx // 2 - 2, nx // 2 + 2)
-    return float(((1.0 - F["fl"]) * F["phi"][0])[:, cols].sum(axis=0).mean())
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16s", "bf16s"])
