@@ -373,6 +373,104 @@ def compare_precision(case, precision, mlups_fp64, front_steps, stream, flush):
     return out
 
 
+def run_batch(args):
+    """The batched droplet sweep: 256 independent sessile drops of sides 128..512 in one
+    batch (FP16 storage unless --precision says otherwise).  A timed call advances every
+    case by --batch-chunk steps; MLUPS = sum of cells x steps / time.  The state (~6 GB)
+    is far larger than L2, so no flush is needed between calls."""
+    import numpy as np
+    import torch
+    from paper_2603_22902_gb300 import build as B
+    from paper_2603_22902_gb300 import workloads as W
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    barrier(world)
+    from paper_2603_22902_gb300 import lbm
+    prec = args.precision if args.precision != "fp64" or args.batch_fp64 else "fp16s"
+    cases = W.batch_sweep()
+    cells = sum(c.cells for c in cases)
+    stream = torch.cuda.current_stream()
+    solvers = [lbm.Solver(c, precision=prec).set_fields() for c in cases]
+    batch = lbm.Batch(solvers)
+    t0 = time.perf_counter()
+    plan = batch.autotune(trial_steps=args.batch_chunk) if args.autotune else batch.plan.as_dict()
+    tune_s = time.perf_counter() - t0
+    chunk = args.batch_chunk
+    calls = max(1, args.steps // chunk)
+    for _ in range(max(1, args.warmup // chunk)):
+        batch.step(chunk)
+    batch.sync()
+    barrier(world)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(calls)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(calls)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall0 = time.perf_counter()
+    for k in range(calls):
+        starts[k].record(stream)
+        batch.step(chunk)
+        ends[k].record(stream)
+    batch.sync()
+    t_wall = time.perf_counter() - t_wall0
+    barrier(world)
+    clk = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    t_ms_max = reduce_max(t_ms, world)
+    steps = calls * chunk
+    nonfinite = sum(s.diagnostics()["nonfinite"] for s in solvers)
+    if nonfinite:
+        raise SystemExit("non-finite state during the batch benchmark")
+    value = world * cells * steps / (t_ms_max * 1e-3) / 1e6
+    mlups_rank = cells * steps / (t_ms * 1e-3) / 1e6
+    hbm_peak, peak_kind = load_peaks()
+    bpl = bytes_per_lu(2, prec)
+    gbs = bpl * mlups_rank * 1e6 / 1e9
+    final_plan = batch.plan.as_dict()
+    kinds_used = {tuple(final_plan["tile"][_class(c)]) for c in cases}
+    launches = calls * len(kinds_used) if final_plan["mode"] == "persistent" else steps * len(kinds_used)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        small = next(c for c in cases if c.nx == 128)
+        mlups_cpu, done, dt = time_oracle(small, 10 ** 6, budget_s=args.cpu_budget)
+        cpu = {"value": round(mlups_cpu, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{done} oracle time steps of {small.name} (FP64, {dt:.1f} s), one host thread"}
+    for s in solvers:
+        s.close()
+    batch.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": round(t_ms_max / steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp16s": "f16-storage/f32", "bf16s": "bf16-storage/f32"}[prec],
+            "data": "synthetic",
+            "config": {"workload": f"batch_sweep_256 ({len(cases)} sessile drops, sides 128-512, seed 4)",
+                       "cells": cells, "N": 2, "precision": prec, "steps_per_call": chunk,
+                       "l2": "not flushed: the state (%.1f GB) is far larger than L2" % (2 * cells * bpl / 2 / 1e9),
+                       "timing": "CUDA events per call", "parallelism": "replicas" if world > 1 else "single GPU"},
+            "plan": final_plan, "autotune_s": round(tune_s, 2),
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(gbs / hbm_peak, 4), "traffic": None, "peak_kind": f"{peak_kind} (copy bandwidth)",
+                         "bytes_per_lu": bpl, "lu_per_call": cells * chunk},
+            "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches, "clocks": clk,
+            "wall_s_timed_loop": round(t_wall, 4),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _class(case):
+    n = case.cells
+    return 0 if n <= 128 * 128 else 1 if n <= 256 * 256 else 2 if n <= 384 * 384 else 3
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,13 +483,20 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--compare", default="fp16s", help="reduced precision timed beside fp64 ('none' to skip)")
     ap.add_argument("--front-steps", type=int, default=15000)
+    ap.add_argument("--batch-chunk", type=int, default=10, help="steps per batch call (batch_sweep_256)")
+    ap.add_argument("--batch-fp64", action="store_true", help="run the batch sweep in FP64")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
-    return run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "batch_sweep_256":
+        return run_batch(args)
+    return run_gpu(args)
 
 
 if __name__ == "__main__":

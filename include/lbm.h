@@ -205,6 +205,78 @@ const char* lbm_last_error(const lbm_handle* h);
 
 void lbm_destroy(lbm_handle* h);
 
+/* ---- batches of independent cases ----------------------------------------------------
+ * Many independent problems, each created by lbm_create (its own grid, phase properties,
+ * thermal parameters and boundary spec, Section 4), advanced together.  The paper solves
+ * one problem at a time; this is a throughput service of the library.
+ * - Every tile of every case is one item of a flat work list, so cases of uneven sizes
+ *   fill the GPU together.
+ * - The per-cell arithmetic is that of lbm_step.
+ * - Each case keeps its own handle. Fields, diagnostics and state I/O go through the
+ *   lbm_* calls on that handle.
+ * - A handle may also be stepped alone between batch steps.
+ * - The batch does not own the handles. They must outlive it. */
+typedef struct lbm_batch lbm_batch;
+
+#define LBM_BATCH_PERSISTENT 0 /* one cooperative launch per tile-shape group and call,
+                                  replayed as a CUDA graph; grid barrier between steps */
+#define LBM_BATCH_PER_STEP 1   /* one launch per tile-shape group and step */
+
+/* Size classes of a case, by cells nx * ny: <= 128^2, <= 256^2, <= 384^2, larger. */
+#define LBM_BATCH_CLASSES 4
+
+typedef struct {
+    int mode;                          /* LBM_BATCH_PERSISTENT or LBM_BATCH_PER_STEP */
+    int blocks_per_sm;                 /* persistent grid: resident blocks per SM, 0 = all that fit */
+    int tile[LBM_BATCH_CLASSES][2];    /* tile (bx, by) per size class: 32x8, 64x4 or 16x16 */
+    int graph;                         /* out: 1 when the persistent launches replay a CUDA graph */
+} lbm_batch_plan;
+
+/* Build a batch over ncases handles, owned by the caller.
+ * - All handles live on the current device and share N and the precision policy.
+ * - Every handle must have been given fields (lbm_set_fields).
+ * - The initial plan is persistent, 32x8 tiles for every class, all blocks that fit.
+ * - Errors: LBM_EINVAL for mixed N or precision, a NULL or repeated handle, or
+ *   ncases < 1; LBM_ESTATE when a handle has no fields; LBM_ENOMEM.
+ * - Messages are in lbm_batch_last_error(NULL). */
+int lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** out);
+
+/* Stream of the batch's launches (a cudaStream_t; NULL = the legacy default stream). */
+int lbm_batch_set_stream(lbm_batch* b, void* stream);
+
+/* Replace the plan. A tile shape that is not 32x8, 64x4 or 16x16 is LBM_EINVAL. */
+int lbm_batch_set_plan(lbm_batch* b, const lbm_batch_plan* plan);
+int lbm_batch_get_plan(const lbm_batch* b, lbm_batch_plan* plan);
+
+/* Advance every case by nsteps steps (Section 3), queued on the batch stream, without
+ * synchronising.
+ * - Each handle's step count and current state follow.
+ * - Work queued on a handle's own stream must be ordered with the batch stream by the
+ *   caller (the same stream for both is simplest).
+ * - In the persistent mode a step waits for every block of its launch. A wait gives up
+ *   after 2^21 polls (about a second; more for groups above 16M cells), and the next
+ *   lbm_batch_sync reports LBM_ETIMEOUT. */
+int lbm_batch_step(lbm_batch* b, long nsteps);
+
+/* Wait for the batch's queued work. Returns LBM_OK, LBM_ETIMEOUT (a grid-barrier wait
+ * gave up; the barrier is reset) or LBM_ECUDA. */
+int lbm_batch_sync(lbm_batch* b);
+
+/* Tune the plan on the current state and set the best one (also written to *best
+ * when best is not NULL).
+ * - Candidates: each launch mode; each tile shape per size class present; fewer
+ *   resident blocks per SM.
+ * - Each candidate is timed over trial_steps steps (>= 1) with CUDA events, after one
+ *   untimed call of the same length.
+ * - The state of every case, and its step count, are restored afterwards.
+ * - Allocates a copy of all states for the duration of the call. Synchronises. */
+int lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_plan* best);
+
+/* Message of the last failing call on b (or of lbm_batch_create when b is NULL). */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+void lbm_batch_destroy(lbm_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,30 +9,10 @@
 #include <string>
 
 #include "../../include/lbm.h"
+#include "lbm_handle.hpp"
 #include "lbm_launch.cuh"
 
 using namespace lbm;
-
-struct lbm_handle {
-    int device = 0;
-    int N = 0, nx = 0, ny = 0;
-    int precision = LBM_FP64;
-    int diag_every = 0;
-    int tile = TILE_32x8;
-    KParams P{};
-    void* pop[2] = {nullptr, nullptr};    // one population set each (rest + moving block)
-    void* aux[2] = {nullptr, nullptr};    // 3 + 2N lagged planes each
-    size_t pop_bytes = 0, aux_bytes = 0;
-    double* io = nullptr;                 // N + 6 planes: staging for host I/O
-    double* diag_partial = nullptr;
-    double* diag_out = nullptr;
-    unsigned long long* dbg = nullptr;    // bounds-check record (LBM_CHECK_BOUNDS builds)
-    int cur = 0;
-    bool ready = false;
-    long long steps = 0;
-    cudaStream_t stream = nullptr;
-    std::string err;
-};
 
 static thread_local std::string g_create_error;
 

@@ -66,6 +66,16 @@ __device__ __forceinline__ const Coef<R>& coef(const KParams& P)
     else return P.f;
 }
 
+// Global loads.  Data that the same launch never writes goes through the read-only
+// (non-coherent) path; a persistent launch that runs several steps reads what other
+// blocks wrote in its previous step, so its loads bypass L1 (cache-global).
+template <bool COH, class T>
+__device__ __forceinline__ T lbm_ld(const T* p)
+{
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+
 // Global-memory access with an optional bounds check.  In LBM_CHECK_BOUNDS builds an
 // out-of-range index is recorded in P.dbg (count, site code, index) and the access is
 // skipped (a load returns 0); nothing traps.  Normal builds compile to the plain access.
@@ -84,16 +94,17 @@ __device__ __forceinline__ T lbm_zero_like(const T*)
 {
     return static_cast<T>(0.0f);
 }
-#define LBM_LD(P_, ptr, idx, lim, site) \
-    (lbm_in_bounds((P_).dbg, (idx), (lim), (site)) ? __ldg((ptr) + (idx)) : lbm_zero_like(ptr))
+#define LBM_LDX(COH, P_, ptr, idx, lim, site) \
+    (lbm_in_bounds((P_).dbg, (idx), (lim), (site)) ? lbm_ld<COH>((ptr) + (idx)) : lbm_zero_like(ptr))
 #define LBM_ST(P_, ptr, idx, lim, site, val)                                  \
     do {                                                                      \
         if (lbm_in_bounds((P_).dbg, (idx), (lim), (site))) (ptr)[idx] = (val); \
     } while (0)
 #else
-#define LBM_LD(P_, ptr, idx, lim, site) __ldg((ptr) + (idx))
+#define LBM_LDX(COH, P_, ptr, idx, lim, site) lbm_ld<COH>((ptr) + (idx))
 #define LBM_ST(P_, ptr, idx, lim, site, val) ((ptr)[idx] = (val))
 #endif
+#define LBM_LD(P_, ptr, idx, lim, site) LBM_LDX(false, P_, ptr, idx, lim, site)
 
 // Plane layout of one population set: f[0..8], g_0[0..8] .. g_{N-1}[0..8], h[0..8].
 __host__ __device__ constexpr int plane_f(int i) { return i; }

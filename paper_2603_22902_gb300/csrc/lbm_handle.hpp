@@ -1,0 +1,31 @@
+// lbm_handle.hpp -- the handle behind lbm_handle* (internal to the library: the C ABI
+// in lbm_capi.cu and the batches in lbm_batch_capi.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_launch.cuh"
+
+struct lbm_handle {
+    int device = 0;
+    int N = 0, nx = 0, ny = 0;
+    int precision = LBM_FP64;
+    int diag_every = 0;
+    int tile = lbm::TILE_32x8;
+    lbm::KParams P{};
+    void* pop[2] = {nullptr, nullptr};    // one population set each (rest + moving block)
+    void* aux[2] = {nullptr, nullptr};    // 3 + 2N lagged planes each
+    size_t pop_bytes = 0, aux_bytes = 0;
+    double* io = nullptr;                 // N + 6 planes: staging for host I/O
+    double* diag_partial = nullptr;
+    double* diag_out = nullptr;
+    unsigned long long* dbg = nullptr;    // bounds-check record (LBM_CHECK_BOUNDS builds)
+    int cur = 0;
+    bool ready = false;
+    long long steps = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+};

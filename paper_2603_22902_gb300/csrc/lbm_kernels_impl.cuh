@@ -3,6 +3,7 @@
 #pragma once
 
 #include "lbm_aux.cuh"
+#include "lbm_batch.cuh"
 #include "lbm_launch.cuh"
 #include "lbm_step.cuh"
 
@@ -67,6 +68,51 @@ cudaError_t launch_diag(const KParams& P, const void* pop, const void* aux, doub
     return cudaGetLastError();
 }
 
+template <int N, int TX, int TY, class Pr>
+static cudaError_t launch_batch_persistent_t(const BatchTable& T, int nsteps, int blocks, cudaStream_t st)
+{
+    BatchTable t = T;
+    int n = nsteps;
+    void* args[] = {(void*)&t, (void*)&n};
+    return cudaLaunchCooperativeKernel((const void*)batch_persistent_kernel<N, TX, TY, Pr>, dim3(blocks),
+                                       dim3(BATCH_NT), args, 0, st);
+}
+
+template <int N, class Pr>
+cudaError_t launch_batch_persistent(const BatchTable& T, int kind, int nsteps, int blocks, cudaStream_t st)
+{
+    switch (kind) {
+        case TILE_64x4: return launch_batch_persistent_t<N, 64, 4, Pr>(T, nsteps, blocks, st);
+        case TILE_16x16: return launch_batch_persistent_t<N, 16, 16, Pr>(T, nsteps, blocks, st);
+        default: return launch_batch_persistent_t<N, 32, 8, Pr>(T, nsteps, blocks, st);
+    }
+}
+
+template <int N, class Pr>
+cudaError_t batch_blocks_per_sm(int kind, int* out)
+{
+    switch (kind) {
+        case TILE_64x4:
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_persistent_kernel<N, 64, 4, Pr>, BATCH_NT, 0);
+        case TILE_16x16:
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_persistent_kernel<N, 16, 16, Pr>, BATCH_NT,
+                                                                 0);
+        default:
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_persistent_kernel<N, 32, 8, Pr>, BATCH_NT, 0);
+    }
+}
+
+template <int N, class Pr>
+cudaError_t launch_batch_step(const BatchTable& T, int kind, int s, cudaStream_t st)
+{
+    switch (kind) {
+        case TILE_64x4: batch_step_kernel<N, 64, 4, Pr><<<T.total_tiles, BATCH_NT, 0, st>>>(T, s); break;
+        case TILE_16x16: batch_step_kernel<N, 16, 16, Pr><<<T.total_tiles, BATCH_NT, 0, st>>>(T, s); break;
+        default: batch_step_kernel<N, 32, 8, Pr><<<T.total_tiles, BATCH_NT, 0, st>>>(T, s); break;
+    }
+    return cudaGetLastError();
+}
+
 #define LBM_INSTANTIATE(N, PR)                                                                                      \
     template cudaError_t launch_step<N, PR>(const KParams&, const void*, void*, const void*, void*, int,           \
                                             cudaStream_t);                                                          \
@@ -74,6 +120,9 @@ cudaError_t launch_diag(const KParams& P, const void* pop, const void* aux, doub
                                               double*, double*, double*, double*, cudaStream_t);                    \
     template cudaError_t launch_init<N, PR>(const KParams&, const double*, const double*, const double*,           \
                                             const double*, void*, void*, cudaStream_t);                             \
-    template cudaError_t launch_diag<N, PR>(const KParams&, const void*, const void*, double*, double*, cudaStream_t);
+    template cudaError_t launch_diag<N, PR>(const KParams&, const void*, const void*, double*, double*, cudaStream_t); \
+    template cudaError_t launch_batch_persistent<N, PR>(const BatchTable&, int, int, int, cudaStream_t);            \
+    template cudaError_t batch_blocks_per_sm<N, PR>(int, int*);                                                     \
+    template cudaError_t launch_batch_step<N, PR>(const BatchTable&, int, int, cudaStream_t);
 
 }  // namespace lbm

@@ -46,6 +46,38 @@ template <int N, class Pr>
 cudaError_t launch_diag(const KParams& P, const void* pop, const void* aux, double* partial, double* out,
                         cudaStream_t st);
 
+// ---- batches of independent cases (lbm_batch.cuh) -----------------------------------
+constexpr int BATCH_NT = 256;   // threads of every batch block (all batch tile shapes)
+
+struct BatchCase {
+    const void* pop[2];
+    void* aux[2];
+    int tiles_x, tiles_y;
+    int tile_kind;          // TILE_32x8, TILE_64x4 or TILE_16x16
+    int first_tile;         // index of the case's first tile in the flat list
+};
+
+struct BatchTable {            // one group of cases sharing a tile shape
+    int total_tiles;
+    const BatchCase* cases;     // [all cases of the batch]
+    const KParams* params;      // [all cases of the batch]
+    const int* tile_case;       // [total_tiles] case of each tile of the group, cases in order
+    unsigned char* parity;      // the set holding the current state of the group's cases
+    unsigned int* bar;          // grid barrier: {arrivals, generation}; arrivals 0 before a launch
+    int* status;                // 0, or 1 when a barrier wait gave up
+    long long spin_limit;       // polls of a barrier wait before it gives up
+};
+
+// One cooperative launch running nsteps steps of the group (tile shape `kind`); blocks
+// must not exceed the resident limit (batch_blocks_per_sm x SMs).
+template <int N, class Pr>
+cudaError_t launch_batch_persistent(const BatchTable& T, int kind, int nsteps, int blocks, cudaStream_t st);
+template <int N, class Pr>
+cudaError_t batch_blocks_per_sm(int kind, int* out);
+// One launch of step s of the group, one block per tile.
+template <int N, class Pr>
+cudaError_t launch_batch_step(const BatchTable& T, int kind, int s, cudaStream_t st);
+
 // Call f(std::integral_constant<int, N>{}, Prec{}) for the runtime phase count and
 // precision id (LBM_FP64 / FP32 / FP16S / BF16S = 0..3).
 template <class F>

@@ -45,6 +45,7 @@ struct PrecFP64 {
     static constexpr double NABS2 = 1e-24;
     static constexpr float NGUARD = 0.0f;
     static constexpr int OCC_THREADS = 512;
+    static constexpr bool COH = false;
 };
 struct PrecFP32 {
     using R = float;
@@ -55,6 +56,7 @@ struct PrecFP32 {
     static constexpr double NABS2 = 1e-10;
     static constexpr float NGUARD = 1e-3f;
     static constexpr int OCC_THREADS = 768;
+    static constexpr bool COH = false;
 };
 struct PrecFP16S {
     using R = float;
@@ -65,6 +67,7 @@ struct PrecFP16S {
     static constexpr double NABS2 = 1e-6;
     static constexpr float NGUARD = 3e-2f;
     static constexpr int OCC_THREADS = 768;
+    static constexpr bool COH = false;
 };
 struct PrecBF16S {
     using R = float;
@@ -75,6 +78,14 @@ struct PrecBF16S {
     static constexpr double NABS2 = 1e-6;
     static constexpr float NGUARD = 3e-2f;
     static constexpr int OCC_THREADS = 768;
+    static constexpr bool COH = false;
+};
+
+// The same policy for a launch that runs several steps (its loads must see what
+// other blocks of the launch wrote: no read-only path).
+template <class Base>
+struct Coherent : Base {
+    static constexpr bool COH = true;
 };
 
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }

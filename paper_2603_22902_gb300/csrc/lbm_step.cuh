@@ -62,8 +62,8 @@ template <class Pr, int KIND>
 __device__ __forceinline__ typename Pr::R ld_pop(const KParams& P, const PopView<Pr>& v, int s, int i, long long c, int site)
 {
     using R = typename Pr::R;
-    if (i == 0) return (R)LBM_LD(P, v.rest, (long long)s * P.S + c, P.rest_elems, site);
-    const auto q = LBM_LD(P, v.move, (long long)(s * 8 + i - 1) * P.S + c, P.move_elems, site);
+    if (i == 0) return (R)LBM_LDX(Pr::COH, P, v.rest, (long long)s * P.S + c, P.rest_elems, site);
+    const auto q = LBM_LDX(Pr::COH, P, v.move, (long long)(s * 8 + i - 1) * P.S + c, P.move_elems, site);
     if constexpr (!Pr::QUANT) {
         return (R)q;
     } else {
@@ -106,8 +106,8 @@ __device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>
 {
     using R = typename Pr::R;
     const long long S = P.S;
-    const R mdm = (R)LBM_LD(P, ain, aux_mdot() * S + c, P.aux_elems, 1);
-    const R Qm = (R)LBM_LD(P, ain, aux_Q() * S + c, P.aux_elems, 2);
+    const R mdm = (R)LBM_LDX(Pr::COH, P, ain, aux_mdot() * S + c, P.aux_elems, 1);
+    const R Qm = (R)LBM_LDX(Pr::COH, P, ain, aux_Q() * S + c, P.aux_elems, 2);
     const R iden = R(1) / (R(1) - R(0.5) * mdm);
     double phd[N];
 #pragma unroll
@@ -209,23 +209,36 @@ __device__ __forceinline__ void push_species(const KParams& P, const PopView<Pr>
 #else
 #define LBM_OCC(Pr) (Pr::OCC_THREADS)
 #endif
+// Shared-memory elements of type R that step_tile needs: phi_p, rho and psi on the
+// tile and its one-cell ring.
+template <int N, int TX, int TY>
+__host__ __device__ constexpr int tile_smem_elems()
+{
+    return (N + 2) * (TX + 2) * (TY + 2);
+}
+
+// One TX x TY tile (tile column bx, row by) of one time step, run by a block of
+// TX * TY threads; smem holds tile_smem_elems<N, TX, TY>() elements of shared memory.
+// Every thread of the block must call it (it holds two block barriers); the caller
+// places a block barrier before smem is used again.
 template <int N, int TX, int TY, bool COLLIDE, class Pr>
-__global__ void __launch_bounds__(TX * TY, (LBM_OCC(Pr) + TX * TY - 1) / (TX * TY))
-fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __restrict__ pout_base,
-                  const typename Pr::TA* __restrict__ ain, typename Pr::TA* __restrict__ aout, ExportPtrs ex)
+__device__ __forceinline__ void step_tile(const KParams& P, const void* __restrict__ pin_base,
+                                          void* __restrict__ pout_base, const typename Pr::TA* __restrict__ ain,
+                                          typename Pr::TA* __restrict__ aout, const ExportPtrs& ex, int bx, int by,
+                                          typename Pr::R* smem)
 {
     using R = typename Pr::R;
     using TA = typename Pr::TA;
     constexpr int W = TX + 2, H = TY + 2, NT = TX * TY, NRING = 2 * W + 2 * TY;
-    __shared__ R s_phi[N][H][W];
-    __shared__ R s_rho[H][W];
-    __shared__ R s_psi[H][W];
+    R (*s_phi)[H][W] = reinterpret_cast<R (*)[H][W]>(smem);          // [N][H][W]
+    R (*s_rho)[W] = reinterpret_cast<R (*)[W]>(smem + N * H * W);    // [H][W]
+    R (*s_psi)[W] = reinterpret_cast<R (*)[W]>(smem + (N + 1) * H * W);
 
     const int nx = P.nx, ny = P.ny;
     const long long S = P.S;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     const int x = x0 + tx, y = y0 + ty;
     const bool owned = x < nx && y < ny;
     const bool xper = P.bc[0] == PERIODIC, yper = P.bc[2] == PERIODIC;
@@ -272,8 +285,8 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
             for (int i = 0; i < 9; ++i) g[p][i] = ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 6);
 #pragma unroll
         for (int i = 0; i < 9; ++i) h[i] = ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 7);
-        const R mdm = (R)LBM_LD(P, ain, aux_mdot() * S + c, P.aux_elems, 8);
-        const R Qm = (R)LBM_LD(P, ain, aux_Q() * S + c, P.aux_elems, 9);
+        const R mdm = (R)LBM_LDX(Pr::COH, P, ain, aux_mdot() * S + c, P.aux_elems, 8);
+        const R Qm = (R)LBM_LDX(Pr::COH, P, ain, aux_Q() * S + c, P.aux_elems, 9);
         const R iden = R(1) / (R(1) - R(0.5) * mdm);
         double phd[N];
 #pragma unroll
@@ -440,7 +453,7 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
     const R usx = rfma(R(0.5), Fx, jx) * irho, usy = rfma(R(0.5), Fy, jy) * irho;
     const R fpx = chi * (C.us[0] - usx), fpy = chi * (C.us[1] - usy);
     const R ux = rfma(R(0.5), fpx, usx), uy = rfma(R(0.5), fpy, usy);
-    const R psim = (R)LBM_LD(P, ain, aux_psi() * S + c, P.aux_elems, 14);
+    const R psim = (R)LBM_LDX(Pr::COH, P, ain, aux_psi() * S + c, P.aux_elems, 14);
     const R mdot = -((psi - psim) + (ux * gsx + uy * gsy)) * irho;
     const R Ssrc = rfma(rho, mdot, ux * grx + uy * gry);
     const R Lxx = rfma(R(2) * ux, Fx, Ssrc * R(1.0 / 3.0));
@@ -498,8 +511,8 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
         const R og = C.omega_g, kg = C.kg, og1 = R(1) - og;
 #pragma unroll
         for (int pp = 0; pp < N; ++pp) {
-            const R Dx = phi[pp] * ux - (R)LBM_LD(P, ain, aux_phiux(pp) * S + c, P.aux_elems, 15);
-            const R Dy = phi[pp] * uy - (R)LBM_LD(P, ain, aux_phiuy(N, pp) * S + c, P.aux_elems, 16);
+            const R Dx = phi[pp] * ux - (R)LBM_LDX(Pr::COH, P, ain, aux_phiux(pp) * S + c, P.aux_elems, 15);
+            const R Dy = phi[pp] * uy - (R)LBM_LDX(Pr::COH, P, ain, aux_phiuy(N, pp) * S + c, P.aux_elems, 16);
             const R b0 = og * phi[pp] + kg * phi[pp] * mdot;
             const R bxv = R(3) * og * phi[pp] * ux + kg * rfma(R(3), Dx, Rx[pp]);
             const R byv = R(3) * og * phi[pp] * uy + kg * rfma(R(3), Dy, Ry[pp]);
@@ -568,6 +581,16 @@ fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __re
         LBM_ST(P, aout, aux_Q() * S + c, P.aux_elems, 33, (TA)Zm);
         LBM_ST(P, aout, aux_psi() * S + c, P.aux_elems, 34, (TA)psi);
     }
+}
+
+// One launch = one time step of one lattice, one block per tile.
+template <int N, int TX, int TY, bool COLLIDE, class Pr>
+__global__ void __launch_bounds__(TX * TY, (LBM_OCC(Pr) + TX * TY - 1) / (TX * TY))
+fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __restrict__ pout_base,
+                  const typename Pr::TA* __restrict__ ain, typename Pr::TA* __restrict__ aout, ExportPtrs ex)
+{
+    __shared__ typename Pr::R smem[tile_smem_elems<N, TX, TY>()];
+    step_tile<N, TX, TY, COLLIDE, Pr>(P, pin_base, pout_base, ain, aout, ex, blockIdx.x, blockIdx.y, smem);
 }
 
 }  // namespace lbm

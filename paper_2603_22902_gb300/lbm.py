@@ -61,6 +61,20 @@ class lbm_diag(ctypes.Structure):
                 ("nonfinite", ctypes.c_longlong), ("steps", ctypes.c_longlong)]
 
 
+LBM_BATCH_PERSISTENT, LBM_BATCH_PER_STEP = 0, 1
+BATCH_CLASSES = 4
+
+
+class lbm_batch_plan(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("tile", (ctypes.c_int * 2) * BATCH_CLASSES), ("graph", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"mode": "persistent" if self.mode == LBM_BATCH_PERSISTENT else "per_step",
+                "blocks_per_sm": self.blocks_per_sm, "tile": [tuple(t) for t in self.tile],
+                "graph": bool(self.graph)}
+
+
 _lib = None
 _lock = threading.Lock()
 _VP = ctypes.c_void_p
@@ -94,8 +108,20 @@ def library():
             lib.lbm_last_error.argtypes = [_VP]
             lib.lbm_last_error.restype = ctypes.c_char_p
             lib.lbm_destroy.argtypes = [_VP]
+            lib.lbm_batch_create.argtypes = [ctypes.c_int, P(_VP), P(_VP)]
+            lib.lbm_batch_set_stream.argtypes = [_VP, _VP]
+            lib.lbm_batch_set_plan.argtypes = [_VP, P(lbm_batch_plan)]
+            lib.lbm_batch_get_plan.argtypes = [_VP, P(lbm_batch_plan)]
+            lib.lbm_batch_step.argtypes = [_VP, ctypes.c_long]
+            lib.lbm_batch_sync.argtypes = [_VP]
+            lib.lbm_batch_autotune.argtypes = [_VP, ctypes.c_int, P(lbm_batch_plan)]
+            lib.lbm_batch_last_error.argtypes = [_VP]
+            lib.lbm_batch_last_error.restype = ctypes.c_char_p
+            lib.lbm_batch_destroy.argtypes = [_VP]
             for name in ("lbm_create", "lbm_set_stream", "lbm_set_fields", "lbm_step", "lbm_get_fields",
-                         "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile"):
+                         "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile",
+                         "lbm_batch_create", "lbm_batch_set_stream", "lbm_batch_set_plan", "lbm_batch_get_plan",
+                         "lbm_batch_step", "lbm_batch_sync", "lbm_batch_autotune"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -187,6 +213,52 @@ def lbm_debug_bounds(h):
 
 def lbm_destroy(h):
     library().lbm_destroy(h)
+
+
+def _bcheck(rc, b=None):
+    if rc != LBM_OK:
+        msg = library().lbm_batch_last_error(b).decode(errors="replace")
+        raise LBMError(rc, msg)
+    return rc
+
+
+def lbm_batch_create(handles):
+    b = _VP()
+    arr = (_VP * len(handles))(*[h.value if isinstance(h, _VP) else h for h in handles])
+    _bcheck(library().lbm_batch_create(len(handles), arr, ctypes.byref(b)))
+    return b
+
+
+def lbm_batch_set_stream(b, stream_ptr):
+    return _bcheck(library().lbm_batch_set_stream(b, stream_ptr), b)
+
+
+def lbm_batch_set_plan(b, plan):
+    return _bcheck(library().lbm_batch_set_plan(b, ctypes.byref(plan)), b)
+
+
+def lbm_batch_get_plan(b):
+    plan = lbm_batch_plan()
+    _bcheck(library().lbm_batch_get_plan(b, ctypes.byref(plan)), b)
+    return plan
+
+
+def lbm_batch_step(b, nsteps):
+    return _bcheck(library().lbm_batch_step(b, int(nsteps)), b)
+
+
+def lbm_batch_sync(b):
+    return _bcheck(library().lbm_batch_sync(b), b)
+
+
+def lbm_batch_autotune(b, trial_steps):
+    plan = lbm_batch_plan()
+    _bcheck(library().lbm_batch_autotune(b, int(trial_steps), ctypes.byref(plan)), b)
+    return plan
+
+
+def lbm_batch_destroy(b):
+    library().lbm_batch_destroy(b)
 
 
 # ---- parameter structures from a case ---------------------------------------
@@ -281,6 +353,58 @@ class Solver:
         if getattr(self, "h", None):
             lbm_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent Solvers advanced together (lbm_batch_*); the Solvers stay usable
+    for fields, diagnostics and state I/O and must outlive the batch."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.torch = torch
+        self.solvers = list(solvers)
+        self.b = lbm_batch_create([s.h for s in self.solvers])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        lbm_batch_set_stream(self.b, ctypes.c_void_p(stream.cuda_stream))
+
+    @property
+    def plan(self):
+        return lbm_batch_get_plan(self.b)
+
+    def set_plan(self, mode=None, blocks_per_sm=None, tiles=None):
+        p = lbm_batch_get_plan(self.b)
+        if mode is not None:
+            p.mode = {"persistent": LBM_BATCH_PERSISTENT, "per_step": LBM_BATCH_PER_STEP}.get(mode, mode)
+        if blocks_per_sm is not None:
+            p.blocks_per_sm = blocks_per_sm
+        if tiles is not None:
+            for k, (bx, by) in enumerate(tiles):
+                p.tile[k][0], p.tile[k][1] = bx, by
+        lbm_batch_set_plan(self.b, p)
+        return self
+
+    def step(self, n=1):
+        lbm_batch_step(self.b, n)
+        return self
+
+    def sync(self):
+        lbm_batch_sync(self.b)
+        return self
+
+    def autotune(self, trial_steps=20):
+        return lbm_batch_autotune(self.b, trial_steps).as_dict()
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -279,3 +279,49 @@ def perturbed(case: Case, seed: int, amp_u: float = 1e-3, amp_T: float = 0.0) ->
         c.T = c.T + amp_T * r[2]
     c.name += f"_perturbed{seed}"
     return c
+
+
+def sessile_cap(nx, ny, R, theta=90.0, ste=0.1, T_wall=-1.0, T0=1.0, name=None, **kw) -> Case:
+    """A drop on the cold wall y = 0 as a circular cap meeting the wall at the contact
+    angle theta (centre at y = -R cos(theta)), with the wall wetting at theta; other
+    parameters as the single-droplet problem (sessile_drop)."""
+    c = sessile_drop(n=nx, ny=ny, R=R, theta=theta, ste=ste, T_wall=T_wall, T0=T0, **kw)
+    X, Y = grid(nx, ny)
+    yc = -R * math.cos(math.radians(theta))
+    r = np.sqrt((X - nx / 2.0) ** 2 + (Y - yc) ** 2)
+    phi1 = tanh_step(R - r, c.eps)
+    c.phi = np.stack([phi1, 1.0 - phi1])
+    c.name = name or f"sessile_cap_{nx}x{ny}_th{theta:.0f}"
+    c.meta.update(yc=yc)
+    return c
+
+
+BATCH_SIDES = (128, 192, 256, 384, 512)
+
+
+def batch_sweep(n_cases=256, seed=4, sides=BATCH_SIDES) -> List[Case]:
+    """The batched droplet sweep: n_cases independent sessile drops.  Per case, in draw
+    order, four uniforms u0..u3 of the seeded stream: side = sides[floor(5 u0)],
+    Ste = U[0.05, 0.5], theta = U[60, 150] deg, T_wall = U[-2, -0.5]; drop radius
+    round(0.2 side) as a cap at theta."""
+    u = uniform(seed, 4 * n_cases)
+    cases = []
+    for k in range(n_cases):
+        side = sides[min(int(u[4 * k] * len(sides)), len(sides) - 1)]
+        ste = 0.05 + 0.45 * u[4 * k + 1]
+        theta = 60.0 + 90.0 * u[4 * k + 2]
+        T_wall = -2.0 + 1.5 * u[4 * k + 3]
+        c = sessile_cap(side, side, float(round(0.2 * side)), theta=theta, ste=ste, T_wall=T_wall,
+                        name=f"batch{k:03d}_{side}")
+        c.meta.update(side=side, ste=ste, theta=theta, T_wall=T_wall)
+        cases.append(c)
+    return cases
+
+
+def small_batch() -> List[Case]:
+    """Cases of uneven sizes, boundaries and parameters (all N = 2) for batch tests."""
+    return [sessile_cap(48, 40, 14.0, theta=70.0, ste=0.2, T_wall=-1.5),
+            film(nx=16, ny=64, h0=32.0),
+            periodic_drop(n=37, R=9.0, ny=29),
+            sessile_cap(70, 44, 16.0, theta=120.0, ste=0.08, T_wall=-0.7),
+            sessile_cap(130, 33, 12.0, theta=95.0, ste=0.4, T_wall=-2.0)]

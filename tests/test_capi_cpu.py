@@ -78,3 +78,15 @@ def test_asymmetric_sigma_rejected(lib):
         lbm.lbm_create(grid, 3, phases, th, bc, num)
     assert e.value.code == lbm.LBM_EINVAL
     assert b"sigma" in lib.lbm_last_error(None)
+
+
+def test_batch_arguments_rejected_before_any_cuda_call(lib):
+    import ctypes
+    out = ctypes.c_void_p()
+    assert lib.lbm_batch_create(0, None, ctypes.byref(out)) == lbm.LBM_EINVAL
+    assert out.value is None
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert lib.lbm_batch_create(2, arr, ctypes.byref(out)) == lbm.LBM_EINVAL
+    assert b"NULL handle" in lib.lbm_batch_last_error(None)
+    assert lib.lbm_batch_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_autotune(None, 1, None) == lbm.LBM_EINVAL
