@@ -205,6 +205,41 @@ const char* lbm_last_error(const lbm_handle* h);
 
 void lbm_destroy(lbm_handle* h);
 
+/* ---- gradients: the adjoint of the FP64 step -------------------------------------------
+ * Loss of the liquid fraction after nsteps steps from given initial fields:
+ *     L = sum_x w(x) (phi_pcm(x) f_l(x) - f_target(x))^2,  w = 1 when weight is NULL,
+ * where phi_pcm = sum_p phi_p over the phases with latent > 0: the liquid fraction of
+ * the phase-changing material (f_l itself jumps from 1 to 0 across a band of width
+ * ~phi_pcm in rho H, so unweighted it has no useful derivative where phi_pcm -> 0);
+ * and its gradient with respect to the parameters of the run: the Dirichlet wall
+ * temperatures (Section 4.1), the latent heat per volume rho_l^p L_p of each phase
+ * (through eq. H; the Stefan number sets L_p = c_p,s (T_m - T_w,ref) / Ste), and the
+ * liquid and solid conductivities of each phase (eq. 2, through tau_h of the enthalpy
+ * LBE, Section 3). */
+typedef struct {
+    double loss;
+    double T_wall[4];                  /* dL / dT_wall[side] (sides without a Dirichlet wall: 0) */
+    double rhoL[LBM_MAXN];             /* dL / d(rho_l^p L_p) */
+    double lambda_s[LBM_MAXN];         /* dL / d lambda_s^p */
+    double lambda_l[LBM_MAXN];         /* dL / d lambda_l^p */
+} lbm_fl_grad;
+
+/* Run the handle from phi0, T0, ux0, uy0 (as lbm_set_fields; ux0 / uy0 may be NULL)
+ * for nsteps steps, then evaluate L and its gradient by the hand-written reverse of
+ * the fused step (discrete adjoint).
+ * - The kinks of eq. H take the derivative of the branch the forward step took.
+ * - The forward run keeps a copy of the state every checkpoint_every steps. The
+ *   reverse sweep recomputes one segment at a time from its checkpoint, stores its
+ *   states, and steps the adjoint back through them.
+ * - Device memory: (nsteps / checkpoint_every + checkpoint_every + 2) states plus
+ *   20 + 11 N planes of doubles, allocated for the duration of the call.
+ * - FP64 handles only (LBM_EINVAL otherwise). fl_target and weight are [ny][nx] like
+ *   the fields, in host or device memory per `where`.
+ * - On return the handle holds the state after nsteps steps. Synchronises. */
+int lbm_adjoint_fl_loss(lbm_handle* h, const double* phi0, const double* T0, const double* ux0,
+                        const double* uy0, const double* fl_target, const double* weight, int where,
+                        long nsteps, int checkpoint_every, lbm_fl_grad* out);
+
 /* ---- batches of independent cases ----------------------------------------------------
  * Many independent problems, each created by lbm_create (its own grid, phase properties,
  * thermal parameters and boundary spec, Section 4), advanced together.  The paper solves

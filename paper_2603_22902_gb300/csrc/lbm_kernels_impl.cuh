@@ -2,6 +2,9 @@
 // (N, precision) pair so that the instantiations compile in parallel.
 #pragma once
 
+#include <algorithm>
+
+#include "lbm_adjoint.cuh"
 #include "lbm_aux.cuh"
 #include "lbm_batch.cuh"
 #include "lbm_launch.cuh"
@@ -112,6 +115,46 @@ cudaError_t launch_batch_step(const BatchTable& T, int kind, int s, cudaStream_t
     }
     return cudaGetLastError();
 }
+
+template <int N>
+cudaError_t launch_adj_mac(const KParams& P, const double* pin, const double* ain, double* mac, cudaStream_t st)
+{
+    const long long blocks = std::min<long long>((P.S + 255) / 256, 65535);
+    mac_kernel<N><<<(int)blocks, 256, 0, st>>>(P, pin, ain, mac);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_adj_cell(const KParams& P, const AdjBufs& B, cudaStream_t st)
+{
+    adj_cell_kernel<N><<<(unsigned)((P.S + 127) / 128), 128, 0, st>>>(P, B);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_adj_moments(const KParams& P, const AdjBufs& B, bool seed, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((P.S + 127) / 128);
+    if (seed) adj_moments_kernel<N, true><<<blocks, 128, 0, st>>>(P, B);
+    else adj_moments_kernel<N, false><<<blocks, 128, 0, st>>>(P, B);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_adj_init(const KParams& P, const double* phi0, const double* T0, const double* apop, double* grad,
+                            cudaStream_t st)
+{
+    const long long blocks = std::min<long long>((P.S + 255) / 256, 65535);
+    adj_init_kernel<N><<<(int)blocks, 256, 0, st>>>(P, phi0, T0, apop, grad);
+    return cudaGetLastError();
+}
+
+#define LBM_INSTANTIATE_ADJ(N)                                                                                    \
+    template cudaError_t launch_adj_mac<N>(const KParams&, const double*, const double*, double*, cudaStream_t); \
+    template cudaError_t launch_adj_cell<N>(const KParams&, const AdjBufs&, cudaStream_t);                         \
+    template cudaError_t launch_adj_moments<N>(const KParams&, const AdjBufs&, bool, cudaStream_t);                \
+    template cudaError_t launch_adj_init<N>(const KParams&, const double*, const double*, const double*, double*,  \
+                                            cudaStream_t);
 
 #define LBM_INSTANTIATE(N, PR)                                                                                      \
     template cudaError_t launch_step<N, PR>(const KParams&, const void*, void*, const void*, void*, int,           \

@@ -78,6 +78,47 @@ cudaError_t batch_blocks_per_sm(int kind, int* out);
 template <int N, class Pr>
 cudaError_t launch_batch_step(const BatchTable& T, int kind, int s, cudaStream_t st);
 
+// ---- adjoint of the FP64 step (lbm_adjoint.cuh) ------------------------------------
+// Gradient slots (planes of the gradient buffer).
+constexpr int GS_TW = 0;                   // T_wall[side], 4 slots
+constexpr int GS_RHOL = 4;                 // rho_l^p L_p (latent heat per volume), MAXN slots
+constexpr int GS_LAMS = 4 + MAXN;          // lambda_s^p
+constexpr int GS_LAML = 4 + 2 * MAXN;      // lambda_l^p
+constexpr int GS_COUNT = 4 + 3 * MAXN;
+
+struct AdjBufs {
+    const double* pin;     // set A populations (FP64 policy layout)
+    const double* ain;     // set A lagged planes
+    const double* bpop;    // adjoint of set B populations
+    const double* baux;    // adjoint of set B lagged planes
+    double* apop;          // adjoint of set A populations (written)
+    double* aaux;          // adjoint of set A lagged planes (written)
+    const double* mac;     // phi_p (N planes), rho, psi of set A
+    double* own;           // phi_p-bar (N planes) and rhoH-bar of each cell's own use
+    double* sb;            // stencil adjoints [k][N + 2][S]
+    double* grad;          // gradient planes [GS_COUNT][S], accumulated
+    const double* fl_target;  // loss seed: target f_l plane (adj_moments_kernel<N, true>)
+    const double* weight;     // loss seed: weight plane, or NULL (weight 1)
+};
+
+// Loss plane after the gradient planes: sum_x w (f_l - f_target)^2 per cell.
+constexpr int GS_LOSS = GS_COUNT;
+
+template <int N>
+cudaError_t launch_adj_mac(const KParams& P, const double* pin, const double* ain, double* mac, cudaStream_t st);
+template <int N>
+cudaError_t launch_adj_cell(const KParams& P, const AdjBufs& B, cudaStream_t st);
+// seed = true: the loss seed at the final state instead of the users' stencil adjoints
+template <int N>
+cudaError_t launch_adj_moments(const KParams& P, const AdjBufs& B, bool seed, cudaStream_t st);
+template <int N>
+cudaError_t launch_adj_init(const KParams& P, const double* phi0, const double* T0, const double* apop, double* grad,
+                            cudaStream_t st);
+// Sums of nplanes planes of S doubles in a fixed order: partial needs nplanes * 256
+// doubles, out nplanes.
+cudaError_t launch_plane_sums(const double* planes, int nplanes, long long S, double* partial, double* out,
+                              cudaStream_t st);
+
 // Call f(std::integral_constant<int, N>{}, Prec{}) for the runtime phase count and
 // precision id (LBM_FP64 / FP32 / FP16S / BF16S = 0..3).
 template <class F>

@@ -75,6 +75,11 @@ class lbm_batch_plan(ctypes.Structure):
                 "graph": bool(self.graph)}
 
 
+class lbm_fl_grad(ctypes.Structure):
+    _fields_ = [("loss", _D), ("T_wall", _D * 4), ("rhoL", _D * MAXN), ("lambda_s", _D * MAXN),
+                ("lambda_l", _D * MAXN)]
+
+
 _lib = None
 _lock = threading.Lock()
 _VP = ctypes.c_void_p
@@ -108,6 +113,8 @@ def library():
             lib.lbm_last_error.argtypes = [_VP]
             lib.lbm_last_error.restype = ctypes.c_char_p
             lib.lbm_destroy.argtypes = [_VP]
+            lib.lbm_adjoint_fl_loss.argtypes = [_VP] + [_VP] * 6 + [ctypes.c_int, ctypes.c_long, ctypes.c_int,
+                                                                     P(lbm_fl_grad)]
             lib.lbm_batch_create.argtypes = [ctypes.c_int, P(_VP), P(_VP)]
             lib.lbm_batch_set_stream.argtypes = [_VP, _VP]
             lib.lbm_batch_set_plan.argtypes = [_VP, P(lbm_batch_plan)]
@@ -121,7 +128,7 @@ def library():
             for name in ("lbm_create", "lbm_set_stream", "lbm_set_fields", "lbm_step", "lbm_get_fields",
                          "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile",
                          "lbm_batch_create", "lbm_batch_set_stream", "lbm_batch_set_plan", "lbm_batch_get_plan",
-                         "lbm_batch_step", "lbm_batch_sync", "lbm_batch_autotune"):
+                         "lbm_batch_step", "lbm_batch_sync", "lbm_batch_autotune", "lbm_adjoint_fl_loss"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -213,6 +220,13 @@ def lbm_debug_bounds(h):
 
 def lbm_destroy(h):
     library().lbm_destroy(h)
+
+
+def lbm_adjoint_fl_loss(h, phi0, T0, ux0, uy0, fl_target, weight, where, nsteps, checkpoint_every):
+    g = lbm_fl_grad()
+    _check(library().lbm_adjoint_fl_loss(h, *[_ptr(a) for a in (phi0, T0, ux0, uy0, fl_target, weight)], where,
+                                         int(nsteps), int(checkpoint_every), ctypes.byref(g)), h)
+    return g
 
 
 def _bcheck(rc, b=None):

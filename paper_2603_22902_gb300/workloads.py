@@ -325,3 +325,48 @@ def small_batch() -> List[Case]:
             periodic_drop(n=37, R=9.0, ny=29),
             sessile_cap(70, 44, 16.0, theta=120.0, ste=0.08, T_wall=-0.7),
             sessile_cap(130, 33, 12.0, theta=95.0, ste=0.4, T_wall=-2.0)]
+
+
+def impurity_freeze(n=512, ny=None, liquid_top=None, T_wall=-1.0, ste=0.2, lam_ratio=1.0, n_disks=24,
+                    r_range=(6, 14), seed=5, T0=0.5, eps=4.0, mobility=0.02, sigma=1e-3) -> Case:
+    """Freezing of a pool holding insoluble impurities (Section 4.4), N = 4: freezing
+    liquid (phase 0) below y = liquid_top (3/4 of the height), a second fluid (phase 1)
+    above, and n_disks seeded, non-overlapping disks of two impurity fluids (phases 2
+    and 3, alternating) in the liquid, kept 2 eps from each other, the walls and the
+    liquid surface.  Walls on all sides; cold Dirichlet bottom, adiabatic elsewhere.
+
+    lam_ratio = lambda_s / lambda_l of phase 0.  Proposed where the paper is silent:
+    upper fluid rho = 1 (as the film problem), impurity conductivities 3 and 1.5 times
+    the liquid's, impurity viscosity 10 times, equal surface tensions, start at T0 = 0.5
+    (above T_m = 0, so that no cell starts on the liquidus kink of eq. H)."""
+    nx, ny = n, (ny or n)
+    top = 0.75 * ny if liquid_top is None else liquid_top
+    X, Y = grid(nx, ny)
+    u = uniform(seed, 8 * n_disks * 64)
+    disks, k, gap = [], 0, 2.0 * eps
+    while len(disks) < n_disks and k + 3 <= len(u):
+        r = r_range[0] + min(int(u[k] * (r_range[1] - r_range[0] + 1)), r_range[1] - r_range[0])
+        cxd = r + gap + u[k + 1] * (nx - 2 * (r + gap))
+        cyd = r + gap + u[k + 2] * (top - 2 * (r + gap))
+        k += 3
+        if all(math.hypot(cxd - a, cyd - b) >= r + rr + gap for a, b, rr in disks):
+            disks.append((cxd, cyd, r))
+    imp = [np.zeros((ny, nx)), np.zeros((ny, nx))]
+    for j, (a, b, r) in enumerate(disks):
+        imp[j % 2] += tanh_step(r - np.sqrt((X - a) ** 2 + (Y - b) ** 2), eps)
+    rest = np.clip(1.0 - imp[0] - imp[1], 0.0, 1.0)
+    liq = tanh_step(top - Y, eps)
+    phi = np.stack([rest * liq, rest * (1.0 - liq), imp[0], imp[1]])
+    lam1 = 0.1
+    phases = [phase(rho_l=1.0, rho_s=0.95, mu_l=0.02, lam_l=lam1, lam_s=lam_ratio * lam1,
+                    latent=latent_from_stefan(ste)),
+              phase(rho_l=1.0, mu_l=0.02, lam_l=lam1),
+              phase(rho_l=1.0, mu_l=0.2, lam_l=3.0 * lam1),
+              phase(rho_l=1.0, mu_l=0.2, lam_l=1.5 * lam1)]
+    sig = np.full((4, 4), sigma)
+    np.fill_diagonal(sig, 0.0)
+    return Case(name=f"impurity_freeze_{nx}x{ny}", nx=nx, ny=ny, N=4, phases=phases, sigma=sig, eps=eps,
+                mobility=mobility, bc=(WALL, WALL, WALL, WALL),
+                tbc=(ADIABATIC, ADIABATIC, DIRICHLET, ADIABATIC), T_wall=(0.0, 0.0, T_wall, 0.0),
+                phi=phi, T=np.full((ny, nx), T0),
+                meta=dict(T_wall=T_wall, ste=ste, lam_ratio=lam_ratio, disks=disks, seed=seed))

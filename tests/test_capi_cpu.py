@@ -90,3 +90,7 @@ def test_batch_arguments_rejected_before_any_cuda_call(lib):
     assert b"NULL handle" in lib.lbm_batch_last_error(None)
     assert lib.lbm_batch_step(None, 1) == lbm.LBM_EINVAL
     assert lib.lbm_batch_autotune(None, 1, None) == lbm.LBM_EINVAL
+
+
+def test_adjoint_arguments_rejected_before_any_cuda_call(lib):
+    assert lib.lbm_adjoint_fl_loss(None, None, None, None, None, None, None, 0, 1, 1, None) == lbm.LBM_EINVAL
