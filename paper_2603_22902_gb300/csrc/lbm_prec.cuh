@@ -55,7 +55,7 @@ struct PrecFP32 {
     static constexpr bool QUANT = false;
     static constexpr double NABS2 = 1e-10;
     static constexpr float NGUARD = 1e-3f;
-    static constexpr int OCC_THREADS = 768;
+    static constexpr int OCC_THREADS = 1024;
     static constexpr bool COH = false;
 };
 struct PrecFP16S {
@@ -66,7 +66,7 @@ struct PrecFP16S {
     static constexpr bool QUANT = true;
     static constexpr double NABS2 = 1e-6;
     static constexpr float NGUARD = 3e-2f;
-    static constexpr int OCC_THREADS = 768;
+    static constexpr int OCC_THREADS = 1024;
     static constexpr bool COH = false;
 };
 struct PrecBF16S {
@@ -77,7 +77,7 @@ struct PrecBF16S {
     static constexpr bool QUANT = true;
     static constexpr double NABS2 = 1e-6;
     static constexpr float NGUARD = 3e-2f;
-    static constexpr int OCC_THREADS = 768;
+    static constexpr int OCC_THREADS = 1024;
     static constexpr bool COH = false;
 };
 

@@ -75,6 +75,33 @@ __device__ __forceinline__ typename Pr::R ld_pop(const KParams& P, const PopView
     }
 }
 
+// The same load for a second read of a population in one step: through the cached
+// (L1) path instead of the read-only one, so that the compiler does not merge it with
+// the first read and keep the value in a register meanwhile.
+template <class Pr, int KIND>
+__device__ __forceinline__ typename Pr::R ld_pop_late(const KParams& P, const PopView<Pr>& v, int s, int i, long long c,
+                                                      int site)
+{
+    using R = typename Pr::R;
+    const long long idx = i == 0 ? (long long)s * P.S + c : (long long)(s * 8 + i - 1) * P.S + c;
+#ifdef LBM_CHECK_BOUNDS
+    if (!lbm_in_bounds(P.dbg, idx, i == 0 ? P.rest_elems : P.move_elems, site)) return R(0);
+#else
+    (void)site;
+#endif
+    if (i == 0) return (R)(Pr::COH ? __ldcg(v.rest + idx) : __ldca(v.rest + idx));
+    const auto q = Pr::COH ? __ldcg(v.move + idx) : __ldca(v.move + idx);
+    if constexpr (!Pr::QUANT) {
+        return (R)q;
+    } else {
+        const float w = (float)wgt(i);
+        const float qf = to_f(q);
+        if (KIND == KIND_F) return qf * (w * F_SCALE);
+        if (KIND == KIND_G) return qf * w;
+        return qf * (w * P.f.E_ref);
+    }
+}
+
 // Store population i of species s at cell c (quantised from R).
 template <class Pr, int KIND>
 __device__ __forceinline__ void st_pop(const KParams& P, const PopView<Pr>& v, int s, int i, long long c,
@@ -270,21 +297,14 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     };
 
     // ---- stage A + B of the own cell --------------------------------------
-    R f[9], g[N][9], h[9];
     R phi[N], rhoH = R(0), fl = R(1), T = R(0), rho = R(1), mu = R(0), lam = R(0), cp = R(1), psi = R(0), chi = R(0);
     // every thread keeps an in-range cell index: loads under `if (owned)` may be
     // issued speculatively, so a thread outside the domain must not form an address
     // past the end of the planes
     const long long c = owned ? (long long)y * nx + x : 0;
+    // The populations are summed here and read again for the collisions below (from
+    // L1), rather than held in registers across the halo stage and its two barriers.
     if (owned) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = ld_pop<Pr, KIND_F>(P, pin, 0, i, c, 5);
-#pragma unroll
-        for (int p = 0; p < N; ++p)
-#pragma unroll
-            for (int i = 0; i < 9; ++i) g[p][i] = ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 6);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) h[i] = ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 7);
         const R mdm = (R)LBM_LDX(Pr::COH, P, ain, aux_mdot() * S + c, P.aux_elems, 8);
         const R Qm = (R)LBM_LDX(Pr::COH, P, ain, aux_Q() * S + c, P.aux_elems, 9);
         const R iden = R(1) / (R(1) - R(0.5) * mdm);
@@ -293,13 +313,13 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         for (int p = 0; p < N; ++p) {
             R s = R(0);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) s += g[p][i];
+            for (int i = 0; i < 9; ++i) s += ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 6);
             phi[p] = s * iden;
             phd[p] = (double)phi[p];
         }
         R sh = R(0);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) sh += h[i];
+        for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 7);
         rhoH = rfma(R(0.5), Qm, sh);
         // eq. H in FP64, the rest of eq. 2 in R
         const Mix<N> m = mixture_map<N>(P, phd);
@@ -438,6 +458,9 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     }
 
     // ---- stage E: flow macroscopics ----------------------------------------
+    R f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = ld_pop_late<Pr, KIND_F>(P, pin, 0, i, c, 5);
     const R jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
     const R jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
     const R sum_f = ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
@@ -511,21 +534,24 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         const R og = C.omega_g, kg = C.kg, og1 = R(1) - og;
 #pragma unroll
         for (int pp = 0; pp < N; ++pp) {
+            R gq[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) gq[i] = ld_pop_late<Pr, KIND_G>(P, pin, 1 + pp, i, c, 6);
             const R Dx = phi[pp] * ux - (R)LBM_LDX(Pr::COH, P, ain, aux_phiux(pp) * S + c, P.aux_elems, 15);
             const R Dy = phi[pp] * uy - (R)LBM_LDX(Pr::COH, P, ain, aux_phiuy(N, pp) * S + c, P.aux_elems, 16);
             const R b0 = og * phi[pp] + kg * phi[pp] * mdot;
             const R bxv = R(3) * og * phi[pp] * ux + kg * rfma(R(3), Dx, Rx[pp]);
             const R byv = R(3) * og * phi[pp] * uy + kg * rfma(R(3), Dy, Ry[pp]);
             R q[9];
-            q[0] = rfma(R(wgt(0)), b0, og1 * g[pp][0]);
-            q[1] = rfma(R(wgt(1)), b0 + bxv, og1 * g[pp][1]);
-            q[3] = rfma(R(wgt(3)), b0 - bxv, og1 * g[pp][3]);
-            q[2] = rfma(R(wgt(2)), b0 + byv, og1 * g[pp][2]);
-            q[4] = rfma(R(wgt(4)), b0 - byv, og1 * g[pp][4]);
-            q[5] = rfma(R(wgt(5)), b0 + (bxv + byv), og1 * g[pp][5]);
-            q[7] = rfma(R(wgt(7)), b0 - (bxv + byv), og1 * g[pp][7]);
-            q[6] = rfma(R(wgt(6)), b0 + (byv - bxv), og1 * g[pp][6]);
-            q[8] = rfma(R(wgt(8)), b0 - (byv - bxv), og1 * g[pp][8]);
+            q[0] = rfma(R(wgt(0)), b0, og1 * gq[0]);
+            q[1] = rfma(R(wgt(1)), b0 + bxv, og1 * gq[1]);
+            q[3] = rfma(R(wgt(3)), b0 - bxv, og1 * gq[3]);
+            q[2] = rfma(R(wgt(2)), b0 + byv, og1 * gq[2]);
+            q[4] = rfma(R(wgt(4)), b0 - byv, og1 * gq[4]);
+            q[5] = rfma(R(wgt(5)), b0 + (bxv + byv), og1 * gq[5]);
+            q[7] = rfma(R(wgt(7)), b0 - (bxv + byv), og1 * gq[7]);
+            q[6] = rfma(R(wgt(6)), b0 + (byv - bxv), og1 * gq[6]);
+            q[8] = rfma(R(wgt(8)), b0 - (byv - bxv), og1 * gq[8]);
             push_species<KIND_G, Pr>(P, pout, 1 + pp, x, y, q);
             LBM_ST(P, aout, aux_phiux(pp) * S + c, P.aux_elems, 30, (TA)(phi[pp] * ux));
             LBM_ST(P, aout, aux_phiuy(N, pp) * S + c, P.aux_elems, 31, (TA)(phi[pp] * uy));
@@ -534,6 +560,9 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
 
     // ---- stage F: enthalpy collision + Dirichlet ghosts ---------------------
     {
+        R h[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) h[i] = ld_pop_late<Pr, KIND_H>(P, pin, N + 1, i, c, 7);
         const R Z = rho * cp * T, E = C.E_ref * T;
         const R kh = rfma(R(-0.5), oh, R(1)), oh1 = R(1) - oh;
         const R Zm = Z * mdot;
