@@ -40,7 +40,7 @@ METRIC = "coupled-step MLUPS and % HBM roofline at 1 GB300; reduced-precision vs
 # 2 [ (N + 2) rest + 8 (N + 2) moving populations + (3 + 2 N) lagged planes ],
 # with (rest, moving, lagged) element sizes of (8, 8, 8) for FP64 (688 B at N = 2),
 # (4, 4, 4) for FP32 and (4, 2, 4) for the 16-bit storage policies.
-ELEM = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "fp16s": (4, 2, 4), "bf16s": (4, 2, 4)}
+ELEM = {"fp64": (8, 8, 8), "df64": (8, 8, 8), "fp32": (4, 4, 4), "fp16s": (4, 2, 4), "bf16s": (4, 2, 4)}
 
 
 def bytes_per_lu(N: int, precision: str = "fp64") -> int:
@@ -317,7 +317,8 @@ def run_gpu(args):
             "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms_max / args.steps, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "fp16s": "f16-storage/f32", "bf16s": "bf16-storage/f32"}[args.precision],
+            "dtype": {"fp64": "f64", "df64": "df64 (f32 pair)", "fp32": "f32", "fp16s": "f16-storage/f32",
+                      "bf16s": "bf16-storage/f32"}[args.precision],
             "data": "synthetic",
             "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "N": N, "precision": args.precision,
                        "l2": "flushed (256 MiB write) before every timed step", "timing": "CUDA events per step",

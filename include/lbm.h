@@ -58,6 +58,8 @@ extern "C" {
 #define LBM_FP32 1  /* FP32 storage and arithmetic */
 #define LBM_FP16S 2 /* FP16 storage of shifted populations, FP32 arithmetic */
 #define LBM_BF16S 3 /* BF16 storage of shifted populations, FP32 arithmetic */
+#define LBM_DF64 4  /* double-word (FP32 pair, ~48-bit) storage and arithmetic on the FP32
+                       pipes, the enthalpy map in FP64; 32x8 tiles only, no batch form */
 
 #define LBM_HOST 0
 #define LBM_DEVICE 1
@@ -104,7 +106,7 @@ typedef struct {
 /* Numerical parameters: interface width eps and mobility M (Section 3:
  * M = c_s^2 (tau_g - 1/2)); pairwise surface tensions sigma[p*LBM_MAXN+q] (symmetric,
  * zero diagonal; beta_pq = 3 sigma_pq / eps, k_pq = -3 eps sigma_pq / 4, Section 2);
- * precision = LBM_FP64 / LBM_FP32 / LBM_FP16S / LBM_BF16S; diag_every = K > 0 makes
+ * precision = LBM_FP64 / LBM_FP32 / LBM_FP16S / LBM_BF16S / LBM_DF64; diag_every = K > 0 makes
  * lbm_step run the non-finite check every K steps (0 = only when asked). */
 typedef struct {
     double eps, mobility;

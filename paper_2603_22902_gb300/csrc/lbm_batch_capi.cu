@@ -361,6 +361,8 @@ int lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** out)
         if (cases[c]->N != cases[0]->N) return bfail(nullptr, LBM_EINVAL, "batch cases must share N");
         if (cases[c]->precision != cases[0]->precision)
             return bfail(nullptr, LBM_EINVAL, "batch cases must share the precision policy");
+        if (cases[c]->precision == LBM_DF64)
+            return bfail(nullptr, LBM_EINVAL, "the LBM_DF64 policy has no batch form");
         if (cases[c]->device != cases[0]->device) return bfail(nullptr, LBM_EINVAL, "batch cases must share a device");
         if (!cases[c]->ready) return bfail(nullptr, LBM_ESTATE, "a batch case has no fields (lbm_set_fields)");
     }

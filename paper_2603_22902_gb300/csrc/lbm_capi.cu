@@ -56,6 +56,17 @@ static void free_all(lbm_handle* h)
     h->dbg = nullptr;
 }
 
+// Double-word copy of the coefficients, for the double-word policy.
+static Coef<df64> split_coef(const Coef<double>& d)
+{
+    static_assert(sizeof(Coef<double>) == sizeof(Coef<df64>), "Coef holds only T members");
+    Coef<df64> x{};
+    const double* src = reinterpret_cast<const double*>(&d);
+    df64* dst = reinterpret_cast<df64*>(&x);
+    for (size_t k = 0; k < sizeof(Coef<double>) / sizeof(double); ++k) dst[k] = df64(src[k]);
+    return x;
+}
+
 // FP32 copy of the coefficients, for the policies that compute in FP32.
 static Coef<float> round_coef(const Coef<double>& d)
 {
@@ -78,8 +89,8 @@ int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_t
     if (grid->nx < 3 || grid->ny < 3) return fail(nullptr, LBM_EINVAL, "nx and ny must be >= 3");
     if ((long long)grid->nx * grid->ny > (1LL << 31)) return fail(nullptr, LBM_EINVAL, "grid too large");
     if (N < 2 || N > LBM_MAXN) return fail(nullptr, LBM_EINVAL, "N must be in [2, 4]");
-    if (num->precision < LBM_FP64 || num->precision > LBM_BF16S)
-        return fail(nullptr, LBM_EINVAL, "precision must be LBM_FP64, LBM_FP32, LBM_FP16S or LBM_BF16S");
+    if (num->precision < LBM_FP64 || num->precision > LBM_DF64)
+        return fail(nullptr, LBM_EINVAL, "precision must be LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S or LBM_DF64");
     if (!(num->eps > 0.0) || !(num->mobility > 0.0)) return fail(nullptr, LBM_EINVAL, "eps and mobility must be > 0");
     if (num->diag_every < 0) return fail(nullptr, LBM_EINVAL, "diag_every must be >= 0");
     if (!(th->T_sol <= th->T_liq)) return fail(nullptr, LBM_EINVAL, "T_sol must be <= T_liq");
@@ -176,6 +187,7 @@ int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_t
     P.aux_elems = (long long)naux_planes(N) * P.S;
     P.d.inv_E_ref = 1.0 / P.d.E_ref;
     P.f = round_coef(P.d);
+    P.x = split_coef(P.d);
     P.dbg = nullptr;
     dispatch(N, h->precision, [&](auto n, auto pr) {
         using Pr = decltype(pr);
@@ -224,6 +236,8 @@ int lbm_set_tile(lbm_handle* h, int bx, int by)
         int tx, ty;
         tile_dims(id, tx, ty);
         if (tx == bx && ty == by) {
+            if (h->precision == LBM_DF64 && id != TILE_32x8)
+                return fail(h, LBM_EINVAL, "the LBM_DF64 policy is compiled for the 32x8 tile only");
             h->tile = id;
             return LBM_OK;
         }

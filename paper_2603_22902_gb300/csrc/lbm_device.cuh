@@ -3,6 +3,9 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+
+#include "lbm_df64.cuh"
 
 namespace lbm {
 
@@ -23,8 +26,9 @@ __device__ __forceinline__ double rrsqrt(double a) { return rsqrt(a); }
 __device__ __forceinline__ float rrsqrt(float a) { return rsqrtf(a); }
 
 // Per-run coefficients used by the arithmetic of the step, in type T.  The host fills
-// a double and a float copy, so a policy computing in FP32 reads float constants and
-// converts nothing per cell (FP64 <-> FP32 conversions share the FP64 unit).
+// a double, a float and a double-word copy, so a policy computing in FP32 or in
+// double-word arithmetic reads its own constants and converts nothing per cell
+// (FP64 <-> FP32 conversions share the FP64 unit).
 template <class T>
 struct Coef {
     // eq. 2 mixture coefficients per phase
@@ -52,6 +56,7 @@ struct KParams {
     int bc[4], tbc[4];            // side kinds, sides 0 x-min, 1 x-max, 2 y-min, 3 y-max
     Coef<double> d;               // coefficients, FP64
     Coef<float> f;                // the same, rounded to FP32
+    Coef<df64> x;                 // the same, as double words (hi + lo)
     double rhoL[MAXN];            // rho_l^p L_p: latent heat per volume of pure phase p
     double T_sol, T_liq;
     long long rest_elems, move_elems; // elements of the rest / moving block of one population set
@@ -62,7 +67,8 @@ struct KParams {
 template <class R>
 __device__ __forceinline__ const Coef<R>& coef(const KParams& P)
 {
-    if constexpr (sizeof(R) == sizeof(double)) return P.d;
+    if constexpr (std::is_same<R, double>::value) return P.d;
+    else if constexpr (std::is_same<R, df64>::value) return P.x;
     else return P.f;
 }
 
@@ -72,8 +78,29 @@ __device__ __forceinline__ const Coef<R>& coef(const KParams& P)
 template <bool COH, class T>
 __device__ __forceinline__ T lbm_ld(const T* p)
 {
-    if constexpr (COH) return __ldcg(p);
-    else return __ldg(p);
+    if constexpr (std::is_same<T, df64>::value) {
+        const float2 v = COH ? __ldcg(reinterpret_cast<const float2*>(p)) : __ldg(reinterpret_cast<const float2*>(p));
+        return df64(v.x, v.y);
+    } else if constexpr (COH) {
+        return __ldcg(p);
+    } else {
+        return __ldg(p);
+    }
+}
+// The same through L1 (ld.ca) where the launch never writes the data, else
+// cache-global: a second read of a value in one step that the compiler must not merge
+// with the first read.
+template <bool COH, class T>
+__device__ __forceinline__ T lbm_ld_l1(const T* p)
+{
+    if constexpr (std::is_same<T, df64>::value) {
+        const float2 v = COH ? __ldcg(reinterpret_cast<const float2*>(p)) : __ldca(reinterpret_cast<const float2*>(p));
+        return df64(v.x, v.y);
+    } else if constexpr (COH) {
+        return __ldcg(p);
+    } else {
+        return __ldca(p);
+    }
 }
 
 // Global-memory access with an optional bounds check.  In LBM_CHECK_BOUNDS builds an

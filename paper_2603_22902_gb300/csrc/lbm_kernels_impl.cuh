@@ -22,15 +22,24 @@ static cudaError_t launch_fused_t(const KParams& P, const void* pin, void* pout,
     return cudaGetLastError();
 }
 
+// The double-word policy is compiled for the 32 x 8 tile only (each shape of its kernel
+// adds much code); lbm_set_tile refuses other shapes for it, and it has no batch form.
+template <class Pr>
+constexpr bool single_shape() { return std::is_same<Pr, PrecDF64>::value; }
+
 template <int N, bool COLLIDE, class Pr>
 static cudaError_t launch_fused(const KParams& P, const void* pin, void* pout, const void* ain, void* aout,
                                 ExportPtrs ex, int tile, cudaStream_t st)
 {
-    switch (tile) {
-        case TILE_32x4: return launch_fused_t<N, 32, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
-        case TILE_64x4: return launch_fused_t<N, 64, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
-        case TILE_16x16: return launch_fused_t<N, 16, 16, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
-        default: return launch_fused_t<N, 32, 8, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
+    if constexpr (single_shape<Pr>()) {
+        return launch_fused_t<N, 32, 8, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
+    } else {
+        switch (tile) {
+            case TILE_32x4: return launch_fused_t<N, 32, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
+            case TILE_64x4: return launch_fused_t<N, 64, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
+            case TILE_16x16: return launch_fused_t<N, 16, 16, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
+            default: return launch_fused_t<N, 32, 8, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
+        }
     }
 }
 
@@ -84,36 +93,48 @@ static cudaError_t launch_batch_persistent_t(const BatchTable& T, int nsteps, in
 template <int N, class Pr>
 cudaError_t launch_batch_persistent(const BatchTable& T, int kind, int nsteps, int blocks, cudaStream_t st)
 {
-    switch (kind) {
-        case TILE_64x4: return launch_batch_persistent_t<N, 64, 4, Pr>(T, nsteps, blocks, st);
-        case TILE_16x16: return launch_batch_persistent_t<N, 16, 16, Pr>(T, nsteps, blocks, st);
-        default: return launch_batch_persistent_t<N, 32, 8, Pr>(T, nsteps, blocks, st);
+    if constexpr (single_shape<Pr>()) {
+        return cudaErrorNotSupported;
+    } else {
+        switch (kind) {
+            case TILE_64x4: return launch_batch_persistent_t<N, 64, 4, Pr>(T, nsteps, blocks, st);
+            case TILE_16x16: return launch_batch_persistent_t<N, 16, 16, Pr>(T, nsteps, blocks, st);
+            default: return launch_batch_persistent_t<N, 32, 8, Pr>(T, nsteps, blocks, st);
+        }
     }
 }
 
 template <int N, class Pr>
 cudaError_t batch_blocks_per_sm(int kind, int* out)
 {
-    switch (kind) {
-        case TILE_64x4:
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_persistent_kernel<N, 64, 4, Pr>, BATCH_NT, 0);
-        case TILE_16x16:
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_persistent_kernel<N, 16, 16, Pr>, BATCH_NT,
-                                                                 0);
-        default:
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_persistent_kernel<N, 32, 8, Pr>, BATCH_NT, 0);
+    if constexpr (single_shape<Pr>()) {
+        return cudaErrorNotSupported;
+    } else {
+        switch (kind) {
+            case TILE_64x4:
+                return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_persistent_kernel<N, 64, 4, Pr>, BATCH_NT, 0);
+            case TILE_16x16:
+                return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_persistent_kernel<N, 16, 16, Pr>, BATCH_NT,
+                                                                     0);
+            default:
+                return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_persistent_kernel<N, 32, 8, Pr>, BATCH_NT, 0);
+        }
     }
 }
 
 template <int N, class Pr>
 cudaError_t launch_batch_step(const BatchTable& T, int kind, int s, cudaStream_t st)
 {
-    switch (kind) {
-        case TILE_64x4: batch_step_kernel<N, 64, 4, Pr><<<T.total_tiles, BATCH_NT, 0, st>>>(T, s); break;
-        case TILE_16x16: batch_step_kernel<N, 16, 16, Pr><<<T.total_tiles, BATCH_NT, 0, st>>>(T, s); break;
-        default: batch_step_kernel<N, 32, 8, Pr><<<T.total_tiles, BATCH_NT, 0, st>>>(T, s); break;
+    if constexpr (single_shape<Pr>()) {
+        return cudaErrorNotSupported;
+    } else {
+        switch (kind) {
+            case TILE_64x4: batch_step_kernel<N, 64, 4, Pr><<<T.total_tiles, BATCH_NT, 0, st>>>(T, s); break;
+            case TILE_16x16: batch_step_kernel<N, 16, 16, Pr><<<T.total_tiles, BATCH_NT, 0, st>>>(T, s); break;
+            default: batch_step_kernel<N, 32, 8, Pr><<<T.total_tiles, BATCH_NT, 0, st>>>(T, s); break;
+        }
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
 }
 
 template <int N>

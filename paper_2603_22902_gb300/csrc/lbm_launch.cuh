@@ -120,7 +120,7 @@ cudaError_t launch_plane_sums(const double* planes, int nplanes, long long S, do
                               cudaStream_t st);
 
 // Call f(std::integral_constant<int, N>{}, Prec{}) for the runtime phase count and
-// precision id (LBM_FP64 / FP32 / FP16S / BF16S = 0..3).
+// precision id (LBM_FP64 / FP32 / FP16S / BF16S / DF64 = 0..4).
 template <class F>
 auto dispatch(int N, int prec, F&& f)
 {
@@ -133,6 +133,7 @@ auto dispatch(int N, int prec, F&& f)
         case 1: return byN(PrecFP32{});
         case 2: return byN(PrecFP16S{});
         case 3: return byN(PrecBF16S{});
+        case 4: return byN(PrecDF64{});
         default: return byN(PrecFP64{});
     }
 }

@@ -32,6 +32,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "lbm_df64.cuh"
+
 namespace lbm {
 
 constexpr float F_SCALE = 1.0f / 4096.0f;
@@ -78,6 +80,22 @@ struct PrecBF16S {
     static constexpr double NABS2 = 1e-6;
     static constexpr float NGUARD = 3e-2f;
     static constexpr int OCC_THREADS = 1024;
+    static constexpr bool COH = false;
+};
+
+// FP64-class accuracy on the FP32 pipes: every population, lagged value and
+// coefficient is a double word (lbm_df64.cuh), 8 bytes like FP64, and the collision
+// arithmetic runs in double-word arithmetic; the eq. H map stays in FP64.  The guard of
+// the pairwise normal is the oracle's.
+struct PrecDF64 {
+    using R = df64;
+    using TR = df64;
+    using TM = df64;
+    using TA = df64;
+    static constexpr bool QUANT = false;
+    static constexpr double NABS2 = 1e-24;
+    static constexpr float NGUARD = 0.0f;
+    static constexpr int OCC_THREADS = 512;
     static constexpr bool COH = false;
 };
 

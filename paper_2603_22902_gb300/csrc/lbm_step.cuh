@@ -89,8 +89,8 @@ __device__ __forceinline__ typename Pr::R ld_pop_late(const KParams& P, const Po
 #else
     (void)site;
 #endif
-    if (i == 0) return (R)(Pr::COH ? __ldcg(v.rest + idx) : __ldca(v.rest + idx));
-    const auto q = Pr::COH ? __ldcg(v.move + idx) : __ldca(v.move + idx);
+    if (i == 0) return (R)lbm_ld_l1<Pr::COH>(v.rest + idx);
+    const auto q = lbm_ld_l1<Pr::COH>(v.move + idx);
     if constexpr (!Pr::QUANT) {
         return (R)q;
     } else {
@@ -159,6 +159,44 @@ __device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>
     psi = fs * mix_sum<N, R>(phi, C.drho);
 }
 
+// Stage A + B of one cell of the tile or its ring: phi_p, rho H, f_l, rho and psi, and T
+// when want_T (the tile's own cells).  The map runs in FP64, the rest of eq. 2 in R.
+template <int N, class Pr>
+__device__ __forceinline__ void cell_moments(const KParams& P, const PopView<Pr>& pin,
+                                             const typename Pr::TA* __restrict__ ain, long long c, bool want_T,
+                                             typename Pr::R (&phi)[N], typename Pr::R& rhoH, typename Pr::R& fl,
+                                             typename Pr::R& T, typename Pr::R& rho, typename Pr::R& psi)
+{
+    using R = typename Pr::R;
+    const long long S = P.S;
+    const R mdm = (R)LBM_LDX(Pr::COH, P, ain, aux_mdot() * S + c, P.aux_elems, 1);
+    const R Qm = (R)LBM_LDX(Pr::COH, P, ain, aux_Q() * S + c, P.aux_elems, 2);
+    const R iden = R(1) / (R(1) - R(0.5) * mdm);
+    double phd[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        R s = R(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s += ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 3);
+        phi[p] = s * iden;
+        phd[p] = (double)phi[p];
+    }
+    R sh = R(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 4);
+    rhoH = rfma(R(0.5), Qm, sh);
+    const Mix<N> m = mixture_map<N>(P, phd);
+    double fld, Td = 0.0;
+    if (want_T) enthalpy_map<N, true>(P, m, (double)rhoH, fld, Td);
+    else enthalpy_map<N, false>(P, m, (double)rhoH, fld, Td);
+    const Coef<R>& C = coef<R>(P);
+    fl = (R)fld;
+    T = (R)Td;
+    const R fs = R(1) - fl;
+    rho = rfma(fs, mix_sum<N, R>(phi, C.rho_s), fl * mix_sum<N, R>(phi, C.rho_l));
+    psi = fs * mix_sum<N, R>(phi, C.drho);
+}
+
 // Push one post-collision population q_j of species s at node (x, y) into set B.
 // Periodic sides wrap; a population leaving through an x wall is reflected into the
 // node's own opposite slot (half-way bounce-back); through a y wall likewise, except
@@ -203,6 +241,19 @@ __device__ __forceinline__ void push_row(const KParams& P, const PopView<Pr>& ou
     st_pop<Pr, KIND>(P, out, s, J, (long long)y * P.nx + tx, v, 13);
 }
 
+// push_row for a direction j known at run time, whose x component is dx.
+template <int KIND, class Pr>
+__device__ __forceinline__ void push_row_at(const KParams& P, const PopView<Pr>& out, int s, int j, int dx, int x,
+                                            int y, typename Pr::R v)
+{
+    int tx = x + dx;
+    if (dx != 0 && (unsigned)tx >= (unsigned)P.nx) {
+        if (P.bc[0] != PERIODIC) return;
+        tx = tx < 0 ? tx + P.nx : tx - P.nx;
+    }
+    st_pop<Pr, KIND>(P, out, s, j, (long long)y * P.nx + tx, v, 13);
+}
+
 // All nine pushes of one species, plus the outflow copies of the boundary rows.
 template <int KIND, class Pr>
 __device__ __forceinline__ void push_species(const KParams& P, const PopView<Pr>& out, int s, int x, int y,
@@ -237,11 +288,11 @@ __device__ __forceinline__ void push_species(const KParams& P, const PopView<Pr>
 #define LBM_OCC(Pr) (Pr::OCC_THREADS)
 #endif
 // Shared-memory elements of type R that step_tile needs: phi_p, rho and psi on the
-// tile and its one-cell ring.
+// tile and its one-cell ring, and rho H, f_l, T of the tile's cells.
 template <int N, int TX, int TY>
 __host__ __device__ constexpr int tile_smem_elems()
 {
-    return (N + 2) * (TX + 2) * (TY + 2);
+    return (N + 2) * (TX + 2) * (TY + 2) + 3 * TX * TY;
 }
 
 // One TX x TY tile (tile column bx, row by) of one time step, run by a block of
@@ -256,10 +307,11 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
 {
     using R = typename Pr::R;
     using TA = typename Pr::TA;
-    constexpr int W = TX + 2, H = TY + 2, NT = TX * TY, NRING = 2 * W + 2 * TY;
+    constexpr int W = TX + 2, H = TY + 2, NT = TX * TY;
     R (*s_phi)[H][W] = reinterpret_cast<R (*)[H][W]>(smem);          // [N][H][W]
     R (*s_rho)[W] = reinterpret_cast<R (*)[W]>(smem + N * H * W);    // [H][W]
     R (*s_psi)[W] = reinterpret_cast<R (*)[W]>(smem + (N + 1) * H * W);
+    R (*s_own)[NT] = reinterpret_cast<R (*)[NT]>(smem + (N + 2) * H * W);  // rho H, f_l, T of the own cells
 
     const int nx = P.nx, ny = P.ny;
     const long long S = P.S;
@@ -272,11 +324,15 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     const PopView<Pr> pin = pop_view<Pr>(P, pin_base);
     const Coef<R>& C = coef<R>(P);
 
-    // The cell coordinates are brought into range before anything else (periodic:
-    // full modulo, since a tile may be wider / taller than the domain; otherwise:
-    // clamped), so no address outside the planes is ever formed, even for a position
+    // ---- stages A + B on the tile and its one-cell ring ----------------------
+    // One code path for all (TX + 2)(TY + 2) positions, so the moments are compiled once.
+    // The cell coordinates are brought into range before anything else (periodic: full
+    // modulo, since a tile may be wider / taller than the domain; otherwise: clamped and
+    // skipped), so no address outside the planes is ever formed, even for a position
     // whose value the ghost rule supplies later.
-    auto halo_at = [&](int lx, int ly) {
+#pragma unroll 1
+    for (int k = tid; k < W * H; k += NT) {
+        const int lx = k % W, ly = k / W;
         int gx = x0 + lx - 1, gy = y0 + ly - 1;
         bool beyond = false;
         if (gx < 0 || gx >= nx) {
@@ -287,68 +343,21 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
             if (yper) gy = wrap_index(gy, ny);
             else { beyond = true; gy = min(max(gy, 0), ny - 1); }
         }
-        if (beyond) return;
-        R ph[N], r, ps;
-        halo_moments<N, Pr>(P, pin, ain, (long long)gy * nx + gx, ph, r, ps);
+        if (beyond) continue;
+        const int ox = lx - 1, oy = ly - 1;
+        const bool own = (unsigned)ox < (unsigned)TX && (unsigned)oy < (unsigned)TY;
+        R ph[N], rH, flv, Tv, r, ps;
+        cell_moments<N, Pr>(P, pin, ain, (long long)gy * nx + gx, own, ph, rH, flv, Tv, r, ps);
 #pragma unroll
         for (int p = 0; p < N; ++p) s_phi[p][ly][lx] = ph[p];
         s_rho[ly][lx] = r;
         s_psi[ly][lx] = ps;
-    };
-
-    // ---- stage A + B of the own cell --------------------------------------
-    R phi[N], rhoH = R(0), fl = R(1), T = R(0), rho = R(1), mu = R(0), lam = R(0), cp = R(1), psi = R(0), chi = R(0);
-    // every thread keeps an in-range cell index: loads under `if (owned)` may be
-    // issued speculatively, so a thread outside the domain must not form an address
-    // past the end of the planes
-    const long long c = owned ? (long long)y * nx + x : 0;
-    // The populations are summed here and read again for the collisions below (from
-    // L1), rather than held in registers across the halo stage and its two barriers.
-    if (owned) {
-        const R mdm = (R)LBM_LDX(Pr::COH, P, ain, aux_mdot() * S + c, P.aux_elems, 8);
-        const R Qm = (R)LBM_LDX(Pr::COH, P, ain, aux_Q() * S + c, P.aux_elems, 9);
-        const R iden = R(1) / (R(1) - R(0.5) * mdm);
-        double phd[N];
-#pragma unroll
-        for (int p = 0; p < N; ++p) {
-            R s = R(0);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) s += ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 6);
-            phi[p] = s * iden;
-            phd[p] = (double)phi[p];
+        if (own) {
+            const int o = oy * TX + ox;
+            s_own[0][o] = rH;
+            s_own[1][o] = flv;
+            s_own[2][o] = Tv;
         }
-        R sh = R(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 7);
-        rhoH = rfma(R(0.5), Qm, sh);
-        // eq. H in FP64, the rest of eq. 2 in R
-        const Mix<N> m = mixture_map<N>(P, phd);
-        double fld, Td;
-        enthalpy_map<N, true>(P, m, (double)rhoH, fld, Td);
-        fl = (R)fld;
-        T = (R)Td;
-        const R fs = R(1) - fl;
-        rho = rfma(fs, mix_sum<N, R>(phi, C.rho_s), fl * mix_sum<N, R>(phi, C.rho_l));
-        mu = rfma(fs, mix_sum<N, R>(phi, C.mu_s), fl * mix_sum<N, R>(phi, C.mu_l));
-        lam = rfma(fs, mix_sum<N, R>(phi, C.lam_s), fl * mix_sum<N, R>(phi, C.lam_l));
-        cp = rfma(fs, mix_sum<N, R>(phi, C.cp_s), fl * mix_sum<N, R>(phi, C.cp_l));
-        psi = fs * mix_sum<N, R>(phi, C.drho);
-        chi = fs * mix_sum<N, R>(phi, C.pcm);
-#pragma unroll
-        for (int p = 0; p < N; ++p) s_phi[p][ty + 1][tx + 1] = phi[p];
-        s_rho[ty + 1][tx + 1] = rho;
-        s_psi[ty + 1][tx + 1] = psi;
-    } else {
-        halo_at(tx + 1, ty + 1);
-    }
-    // ---- halo ring ---------------------------------------------------------
-    for (int k = tid; k < NRING; k += NT) {
-        int lx, ly;
-        if (k < W) { lx = k; ly = 0; }
-        else if (k < 2 * W) { lx = k - W; ly = H - 1; }
-        else if (k < 2 * W + TY) { lx = 0; ly = k - 2 * W + 1; }
-        else { lx = W - 1; ly = k - 2 * W - TY + 1; }
-        halo_at(lx, ly);
     }
     __syncthreads();
     // ---- ghosts beyond walls / outflows ------------------------------------
@@ -384,8 +393,21 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     __syncthreads();
     if (!owned) return;
 
-    // ---- stage C: isotropic stencils ---------------------------------------
+    // ---- own cell: the rest of eq. 2 -------------------------------------------
     const int lx = tx + 1, ly = ty + 1;
+    const long long c = (long long)y * nx + x;
+    R phi[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) phi[p] = s_phi[p][ly][lx];
+    const R rhoH = s_own[0][tid], fl = s_own[1][tid], T = s_own[2][tid];
+    const R rho = s_rho[ly][lx], psi = s_psi[ly][lx];
+    const R fs = R(1) - fl;
+    const R mu = rfma(fs, mix_sum<N, R>(phi, C.mu_s), fl * mix_sum<N, R>(phi, C.mu_l));
+    const R lam = rfma(fs, mix_sum<N, R>(phi, C.lam_s), fl * mix_sum<N, R>(phi, C.lam_l));
+    const R cp = rfma(fs, mix_sum<N, R>(phi, C.cp_s), fl * mix_sum<N, R>(phi, C.cp_l));
+    const R chi = fs * mix_sum<N, R>(phi, C.pcm);
+
+    // ---- stage C: isotropic stencils ---------------------------------------
     R gpx[N], gpy[N], lap[N];
     auto grad = [&](R (*a)[W], R& gx_, R& gy_) {
         const R e = a[ly][lx + 1], w = a[ly][lx - 1], n = a[ly + 1][lx], s = a[ly - 1][lx];
@@ -532,7 +554,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     // ---- stage F: phase-field collisions -------------------------------------
     {
         const R og = C.omega_g, kg = C.kg, og1 = R(1) - og;
-#pragma unroll
+#pragma unroll 1
         for (int pp = 0; pp < N; ++pp) {
             R gq[9];
 #pragma unroll
@@ -585,24 +607,26 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         // outflow rows are copied inside push_species; Dirichlet rows get their
         // incoming populations from the ghost rule below
         push_species<KIND_H, Pr>(P, pout, N + 1, x, y, q);
-        // equilibrium of direction j != 0 (for the ghost rule)
-        auto heq = [&](int j) {
-            const R cu = R(cx(j)) * ux + R(cy(j)) * uy;
-            return R(wgt(j)) * rfma(Z, rfma(R(4.5) * cu, cu, rfma(R(3), cu, R(-1.5) * uu)), E);
-        };
-        // Dirichlet wall: ghost behind the half-way wall with T_g = 2 T_w - T, u = 0;
-        // its post-collision population is h_eq(ghost) + (1 - 1/tau_h)(h_j - h_eq_j).
-        if (y == 0 && P.bc[2] == WALL && P.tbc[2] == DIRICHLET) {
-            const R Eg = C.E_ref * (R(2) * C.Tw[2] - T);
-            push_row<2, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[2] - heq(2), R(wgt(2)) * Eg));
-            push_row<5, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[5] - heq(5), R(wgt(5)) * Eg));
-            push_row<6, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[6] - heq(6), R(wgt(6)) * Eg));
-        }
-        if (y == ny - 1 && P.bc[3] == WALL && P.tbc[3] == DIRICHLET) {
-            const R Eg = C.E_ref * (R(2) * C.Tw[3] - T);
-            push_row<4, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[4] - heq(4), R(wgt(4)) * Eg));
-            push_row<7, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[7] - heq(7), R(wgt(7)) * Eg));
-            push_row<8, KIND_H, Pr>(P, pout, N + 1, x, y, rfma(oh1, h[8] - heq(8), R(wgt(8)) * Eg));
+        // Dirichlet wall: ghost behind the half-way wall with T_g = 2 T_w - T, u = 0; its
+        // post-collision population is h_eq(ghost) + (1 - 1/tau_h)(h_j - h_eq_j) for the
+        // three directions j that enter the boundary row (one code path for both walls:
+        // directions (0, sy), (1, sy), (-1, sy), sy = +1 at the bottom, -1 at the top).
+        const int dside = (y == 0 && P.bc[2] == WALL && P.tbc[2] == DIRICHLET)        ? 2
+                          : (y == ny - 1 && P.bc[3] == WALL && P.tbc[3] == DIRICHLET) ? 3
+                                                                                       : -1;
+        if (dside >= 0) {
+            const bool top = dside == 3;
+            const R vy = top ? -uy : uy;
+            const R Eg = C.E_ref * (R(2) * C.Tw[dside] - T);
+            // equilibrium of a moving direction with weight w and c_j . u = cu
+            auto heq = [&](R w, R cu) { return w * rfma(Z, rfma(R(4.5) * cu, cu, rfma(R(3), cu, R(-1.5) * uu)), E); };
+            const R wa = R(wgt(2)), wd = R(wgt(5));
+            push_row_at<KIND_H, Pr>(P, pout, N + 1, top ? 4 : 2, 0, x, y,
+                                    rfma(oh1, (top ? h[4] : h[2]) - heq(wa, vy), wa * Eg));
+            push_row_at<KIND_H, Pr>(P, pout, N + 1, top ? 8 : 5, 1, x, y,
+                                    rfma(oh1, (top ? h[8] : h[5]) - heq(wd, ux + vy), wd * Eg));
+            push_row_at<KIND_H, Pr>(P, pout, N + 1, top ? 7 : 6, -1, x, y,
+                                    rfma(oh1, (top ? h[7] : h[6]) - heq(wd, vy - ux), wd * Eg));
         }
 
         // ---- stage G: lagged planes ------------------------------------------

@@ -26,9 +26,9 @@ MAXN = 4
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_OUTFLOW = 0, 1, 2
 LBM_T_ADIABATIC, LBM_T_DIRICHLET = 0, 1
-LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S = 0, 1, 2, 3
+LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S, LBM_DF64 = 0, 1, 2, 3, 4
 LBM_HOST, LBM_DEVICE = 0, 1
-PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S, "df64": LBM_DF64}
 
 _D = ctypes.c_double
 

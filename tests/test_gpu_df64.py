@@ -1,0 +1,125 @@
+"""The double-word policy (LBM_DF64: every population, lagged value and coefficient a
+pair of FP32 numbers, ~48 significant bits, arithmetic on the FP32 pipes, eq. H in
+FP64) against the CPU oracle, with the bar of the FP64 path: max |GPU - oracle| <= 1e-10
+on every exported field after 1000 steps of the small cases (several tiles, ragged
+tails, every boundary kind, N = 2, 3, 4), and after a few steps of the full 512 x 512
+sessile drop in the launch configuration that the benchmark times.
+
+The droplet cases whose gas amplifies round-off (see test_gpu_parity) hold the bar up
+to step 150; at 1000 steps the double-word run must stay within 10x the oracle's own
+divergence under a relative perturbation of one temperature by 2^-46 (four units of the
+double-word rounding u^2 = 2^-48), and the conserved sums must match to 1e-10."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_22902_gb300 import workloads as W
+from tests._cases import sensitive_cases, small_cases
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+FIELDS = ("phi", "T", "H", "fl", "ux", "uy", "p")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for the gpu tests")
+    from paper_2603_22902_gb300 import build as B
+    B.build()
+    from paper_2603_22902_gb300 import lbm as L
+    return L
+
+
+def errors(G, O):
+    out = {}
+    for k in FIELDS:
+        scale = max(1.0, float(np.abs(O[k]).max())) if k == "H" else 1.0
+        out[k] = float(np.abs(G[k] - O[k]).max()) / scale
+    return out
+
+
+def run_df64(L, case, steps):
+    s = L.Solver(case, precision="df64").set_fields()
+    s.step(steps)
+    G = s.fields_numpy()
+    d = s.diagnostics()
+    s.close()
+    return G, d
+
+
+@pytest.mark.parametrize("name", list(small_cases().keys()))
+def test_df64_parity_1000_steps(lbm, name):
+    case = small_cases()[name]
+    G, d = run_df64(lbm, case, 1000)
+    O = oracle.Oracle(case).step(1000).fields()
+    errs = errors(G, O)
+    print(name, errs)
+    assert d["nonfinite"] == 0
+    assert all(v <= TOL for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("name", list(sensitive_cases().keys()))
+def test_df64_round_off_sensitive_droplets(lbm, name):
+    case = sensitive_cases()[name]
+    G, _ = run_df64(lbm, case, 150)
+    errs = errors(G, oracle.Oracle(case).step(150).fields())
+    print(name, "150 steps", errs)
+    assert all(v <= TOL for v in errs.values()), errs
+    G, d = run_df64(lbm, case, 1000)
+    pert = case.copy()
+    pert.T = pert.T.copy()
+    pert.T[case.ny // 2, case.nx // 2] *= 1.0 + 2.0 ** -46
+    O, Op = oracle.Oracle(case).step(1000).fields(), oracle.Oracle(pert).step(1000).fields()
+    report = {}
+    for k in FIELDS:
+        floor = float(np.abs(O[k] - Op[k]).max())
+        err = float(np.abs(G[k] - O[k]).max())
+        report[k] = (err, floor)
+    print(name, "1000 steps (err, floor)", report)
+    for k, (err, floor) in report.items():
+        assert err <= max(TOL, 10.0 * floor), (k, err, floor)
+    fs = 1.0 - O["fl"]
+    for p in range(case.N):
+        assert abs(d["mass"][p] - O["phi"][p].sum()) <= 1e-10 * O["phi"][p].sum()
+        assert abs(d["solid"][p] - (fs * O["phi"][p]).sum()) <= 1e-8
+
+
+def test_df64_full_size_sessile_drop(lbm):
+    # the benchmark's workload and launch configuration (512 x 512, 32 x 8 tiles)
+    case = W.sessile_drop()
+    G, d = run_df64(lbm, case, 12)
+    errs = errors(G, oracle.Oracle(case).step(12).fields())
+    print("sessile 512 x 512, 12 steps", errs)
+    assert d["nonfinite"] == 0
+    assert all(v <= TOL for v in errs.values()), errs
+
+
+def test_df64_mass_conserved_without_freezing(lbm):
+    # no latent heat anywhere: sum_x phi_p is conserved by the scheme up to rounding
+    case = W.perturbed(W.periodic_drop(n=64, R=15.0, rho_gas=0.1, sigma=2e-3), seed=2, amp_u=1e-3)
+    for ph in case.phases:
+        ph["latent"] = 0.0
+    s = lbm.Solver(case, precision="df64").set_fields()
+    m0 = s.diagnostics()["mass"]
+    s.step(2000)
+    m1 = s.diagnostics()["mass"]
+    s.close()
+    for a, b in zip(m0, m1):
+        assert abs(b - a) <= 1e-11 * abs(a), (a, b)
+
+
+def test_df64_interface_limits(lbm):
+    case = W.film(nx=16, ny=64, h0=32.0)
+    s = lbm.Solver(case, precision="df64")
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_set_tile(s.h, 64, 4)
+    assert e.value.code == lbm.LBM_EINVAL
+    lbm.lbm_set_tile(s.h, 32, 8)
+    s.set_fields()
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Batch([s])
+    assert e.value.code == lbm.LBM_EINVAL
+    s.close()

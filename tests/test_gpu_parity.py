@@ -21,6 +21,7 @@ import pytest
 
 import oracle
 from paper_2603_22902_gb300 import workloads as W
+from tests._cases import sensitive_cases, small_cases
 
 pytestmark = pytest.mark.gpu
 
@@ -56,31 +57,6 @@ def run_pair(L, case, steps, tile=None):
     s.close()
     O = oracle.Oracle(case).step(steps).fields()
     return G, O
-
-
-def sensitive_cases():
-    return {"sessile_60deg_48x40": W.sessile_drop(n=48, R=14.0, theta=60.0, ny=40),
-            "sessile_90deg_70x44": W.sessile_drop(n=70, R=20.0, theta=90.0, ny=44)}
-
-
-def small_cases():
-    film = W.film(nx=16, ny=256)
-    drop = W.perturbed(W.periodic_drop(n=37, R=9.0, rho_gas=0.2, sigma=2e-3, ny=29), seed=1, amp_u=1e-3)
-    comp = W.compound_drop(n=44, R_core=8.0, R_shell=15.0, ny=36, noise=1e-3)
-    pool = W.lateral_pool(n=33)
-    quad = W.periodic_drop(n=30, R=7.0, N=4, rho_gas=0.5, sigma=1e-3)
-    quad.phi[2] = 0.3 * quad.phi[1]
-    quad.phi[3] = 0.2 * quad.phi[1]
-    quad.phi[1] = 0.5 * quad.phi[1]
-    quad.phases[2]["latent"] = 4.0
-    quad.phases[2]["rho_s"] = 0.9
-    quad.bc = (W.WALL, W.WALL, W.WALL, W.WALL)
-    quad.tbc = (W.ADIABATIC, W.ADIABATIC, W.DIRICHLET, W.ADIABATIC)
-    quad.T_wall = (0.0, 0.0, -0.5, 0.0)
-    quad.T = np.full((quad.ny, quad.nx), 0.2)
-    quad = W.perturbed(quad, seed=4, amp_u=5e-4)
-    return {"film_16x256": film, "periodic_drop_37x29": drop,
-            "compound_N3_44x36": comp, "lateral_pool_N3_walls_33": pool, "N4_walls_30": quad}
 
 
 @pytest.mark.parametrize("name", list(small_cases().keys()))

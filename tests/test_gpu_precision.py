@@ -58,7 +58,7 @@ def test_reduced_precision_front_position(lbm):
     case = W.sessile_drop()
     steps = 15000
     res = {}
-    for prec in ("fp64", "fp32", "fp16s", "bf16s"):
+    for prec in ("fp64", "df64", "fp32", "fp16s", "bf16s"):
         s = lbm.Solver(case, precision=prec).set_fields()
         s.step(steps)
         F = s.fields_numpy()
@@ -69,12 +69,12 @@ def test_reduced_precision_front_position(lbm):
     F64, s64, _ = res["fp64"]
     assert s64 > 5.0                         # the front has moved
     report = {}
-    for prec in ("fp32", "fp16s", "bf16s"):
+    for prec in ("df64", "fp32", "fp16s", "bf16s"):
         F, sf, d = res[prec]
         report[prec] = {"front": sf, "front_err": abs(sf - s64),
                         "phi_max": float(np.abs(F["phi"] - F64["phi"]).max()),
                         "T_max": float(np.abs(F["T"] - F64["T"]).max()),
                         "solid_rel": abs(d["solid"][0] / res["fp64"][2]["solid"][0] - 1.0)}
     print("front fp64", s64, report)
-    for prec in ("fp32", "fp16s"):
+    for prec in ("df64", "fp32", "fp16s"):
         assert report[prec]["front_err"] <= 0.5, (prec, report[prec])
