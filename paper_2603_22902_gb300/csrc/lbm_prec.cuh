@@ -27,6 +27,11 @@
 // changes by O(1) over the interface width, |grad phi_pq| ~ 1/eps, even in the tails);
 // 1e-3 for 16-bit storage, whose rounding noise in phi is ~1e-4 (the normal is then zero
 // only in far tails, where 4 phi_p phi_q / eps < 1e-3 as well).
+//
+// COMPACT: compile the step for a small code footprint rather than for the most
+// instruction-level parallelism (the phase-field collision loop is not unrolled).  The
+// double-word policy needs it: its arithmetic is ~10 instructions per operation, and
+// the fully unrolled step does not fit the instruction cache.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -48,6 +53,7 @@ struct PrecFP64 {
     static constexpr float NGUARD = 0.0f;
     static constexpr int OCC_THREADS = 512;
     static constexpr bool COH = false;
+    static constexpr bool COMPACT = false;
 };
 struct PrecFP32 {
     using R = float;
@@ -59,6 +65,7 @@ struct PrecFP32 {
     static constexpr float NGUARD = 1e-3f;
     static constexpr int OCC_THREADS = 1024;
     static constexpr bool COH = false;
+    static constexpr bool COMPACT = false;
 };
 struct PrecFP16S {
     using R = float;
@@ -70,6 +77,7 @@ struct PrecFP16S {
     static constexpr float NGUARD = 3e-2f;
     static constexpr int OCC_THREADS = 1024;
     static constexpr bool COH = false;
+    static constexpr bool COMPACT = false;
 };
 struct PrecBF16S {
     using R = float;
@@ -81,6 +89,7 @@ struct PrecBF16S {
     static constexpr float NGUARD = 3e-2f;
     static constexpr int OCC_THREADS = 1024;
     static constexpr bool COH = false;
+    static constexpr bool COMPACT = false;
 };
 
 // FP64-class accuracy on the FP32 pipes: every population, lagged value and
@@ -97,6 +106,7 @@ struct PrecDF64 {
     static constexpr float NGUARD = 0.0f;
     static constexpr int OCC_THREADS = 512;
     static constexpr bool COH = false;
+    static constexpr bool COMPACT = true;
 };
 
 // The same policy for a launch that runs several steps (its loads must see what

@@ -159,11 +159,13 @@ __device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>
     psi = fs * mix_sum<N, R>(phi, C.drho);
 }
 
-// Stage A + B of one cell of the tile or its ring: phi_p, rho H, f_l, rho and psi, and T
-// when want_T (the tile's own cells).  The map runs in FP64, the rest of eq. 2 in R.
+// Stage A + B of one cell of the tile or its ring: phi_p, rho H, f_l, T, rho and psi.
+// The map runs in FP64, the rest of eq. 2 in R.  T is needed only for the tile's own
+// cells, but almost every warp holds both kinds, so it is computed for all (a branch on
+// the kind would run both versions of the map).
 template <int N, class Pr>
 __device__ __forceinline__ void cell_moments(const KParams& P, const PopView<Pr>& pin,
-                                             const typename Pr::TA* __restrict__ ain, long long c, bool want_T,
+                                             const typename Pr::TA* __restrict__ ain, long long c,
                                              typename Pr::R (&phi)[N], typename Pr::R& rhoH, typename Pr::R& fl,
                                              typename Pr::R& T, typename Pr::R& rho, typename Pr::R& psi)
 {
@@ -186,9 +188,8 @@ __device__ __forceinline__ void cell_moments(const KParams& P, const PopView<Pr>
     for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 4);
     rhoH = rfma(R(0.5), Qm, sh);
     const Mix<N> m = mixture_map<N>(P, phd);
-    double fld, Td = 0.0;
-    if (want_T) enthalpy_map<N, true>(P, m, (double)rhoH, fld, Td);
-    else enthalpy_map<N, false>(P, m, (double)rhoH, fld, Td);
+    double fld, Td;
+    enthalpy_map<N, true>(P, m, (double)rhoH, fld, Td);
     const Coef<R>& C = coef<R>(P);
     fl = (R)fld;
     T = (R)Td;
@@ -347,7 +348,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         const int ox = lx - 1, oy = ly - 1;
         const bool own = (unsigned)ox < (unsigned)TX && (unsigned)oy < (unsigned)TY;
         R ph[N], rH, flv, Tv, r, ps;
-        cell_moments<N, Pr>(P, pin, ain, (long long)gy * nx + gx, own, ph, rH, flv, Tv, r, ps);
+        cell_moments<N, Pr>(P, pin, ain, (long long)gy * nx + gx, ph, rH, flv, Tv, r, ps);
 #pragma unroll
         for (int p = 0; p < N; ++p) s_phi[p][ly][lx] = ph[p];
         s_rho[ly][lx] = r;
@@ -554,7 +555,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     // ---- stage F: phase-field collisions -------------------------------------
     {
         const R og = C.omega_g, kg = C.kg, og1 = R(1) - og;
-#pragma unroll 1
+#pragma unroll(Pr::COMPACT ? 1 : N)
         for (int pp = 0; pp < N; ++pp) {
             R gq[9];
 #pragma unroll
