@@ -10,8 +10,8 @@
 // "Tight and rigorous error bounds for basic building blocks of double-word
 // arithmetic", ACM TOMS 44 (2017):
 //   sum       -- SloppyDWPlusDW (error <= ~3u^2 (|x| + |y|), u = 2^-24);
-//   product   -- DWTimesDW3 (relative error <= 4u^2);
-//   x * float -- DWTimesFP3 (relative error <= 2u^2);
+//   product   -- DWTimesDW2 without the final renormalisation (relative error ~4u^2);
+//   x * float -- DWTimesFP1 likewise (relative error ~2u^2);
 //   quotient  -- DWDivDW2, with one correctly rounded reciprocal of the divisor's high word.
 // The reciprocal square root is one FP32 Newton step on rsqrtf, then one Newton step
 // with the residual 1 - x y^2 evaluated in double-word arithmetic (tiny arguments are
@@ -78,19 +78,23 @@ __device__ __forceinline__ df64 operator+(df64 x, df64 y)
 }
 __device__ __forceinline__ df64 operator-(df64 x, df64 y) { return x + (-y); }
 
+// Products are left unnormalised: hi is the rounded product of the high words and lo
+// collects its exact rounding error plus the cross terms, so |lo| <= ~3u |hi| instead of
+// u/2 |hi|.  Every operation here takes such pairs as they are (a sum starts with the
+// exact 2Sum of the high words and then renormalises), and the dropped lo.lo term and
+// the two roundings of lo keep the relative error near 4u^2 (DWTimesDW2 of Joldes et al.
+// without its final Fast2Sum).  4 FP32 instructions instead of 9.
 __device__ __forceinline__ df64 operator*(df64 x, df64 y)
 {
-    const df64 c = dw_2prod(x.hi, y.hi);
-    const float t0 = __fmul_rn(x.lo, y.lo);
-    const float t1 = __fmaf_rn(x.hi, y.lo, t0);
-    const float c2 = __fmaf_rn(x.lo, y.hi, t1);
-    return dw_fast2sum(c.hi, __fadd_rn(c.lo, c2));
+    const float p = __fmul_rn(x.hi, y.hi);
+    const float e = __fmaf_rn(x.hi, y.hi, -p);
+    return df64(p, __fmaf_rn(x.lo, y.hi, __fmaf_rn(x.hi, y.lo, e)));
 }
-// x times a float
+// x times a float, unnormalised likewise (3 instructions)
 __device__ __forceinline__ df64 operator*(df64 x, float y)
 {
-    const df64 c = dw_2prod(x.hi, y);
-    return dw_fast2sum(c.hi, __fmaf_rn(x.lo, y, c.lo));
+    const float p = __fmul_rn(x.hi, y);
+    return df64(p, __fmaf_rn(x.lo, y, __fmaf_rn(x.hi, y, -p)));
 }
 __device__ __forceinline__ df64 operator*(float y, df64 x) { return x * y; }
 
@@ -118,6 +122,9 @@ __device__ __forceinline__ bool operator>=(df64 a, df64 b) { return !(a < b); }
 
 // a b + c
 __device__ __forceinline__ df64 rfma(df64 a, df64 b, df64 c) { return a * b + c; }
+__device__ __forceinline__ df64 rfma(float a, df64 b, df64 c) { return b * a + c; }
+__device__ __forceinline__ df64 rfma(df64 a, df64 b, float c) { return a * b + df64(c); }
+__device__ __forceinline__ df64 rfma(df64 a, float b, df64 c) { return a * b + c; }
 
 // 1 / sqrt(x) for x > 0.  An argument below 2^-60 is first scaled by 2^100 (exact), so
 // that y^2 below stays in range; the result is scaled back by 2^50.

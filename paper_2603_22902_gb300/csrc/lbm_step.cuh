@@ -170,10 +170,11 @@ __device__ __forceinline__ void cell_moments(const KParams& P, const PopView<Pr>
                                              typename Pr::R& T, typename Pr::R& rho, typename Pr::R& psi)
 {
     using R = typename Pr::R;
+    using K = exact_t<R>;
     const long long S = P.S;
     const R mdm = (R)LBM_LDX(Pr::COH, P, ain, aux_mdot() * S + c, P.aux_elems, 1);
     const R Qm = (R)LBM_LDX(Pr::COH, P, ain, aux_Q() * S + c, P.aux_elems, 2);
-    const R iden = R(1) / (R(1) - R(0.5) * mdm);
+    const R iden = R(1) / (R(1) - K(0.5) * mdm);
     double phd[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) {
@@ -186,7 +187,7 @@ __device__ __forceinline__ void cell_moments(const KParams& P, const PopView<Pr>
     R sh = R(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 4);
-    rhoH = rfma(R(0.5), Qm, sh);
+    rhoH = rfma(K(0.5), Qm, sh);
     const Mix<N> m = mixture_map<N>(P, phd);
     double fld, Td;
     enthalpy_map<N, true>(P, m, (double)rhoH, fld, Td);
@@ -307,6 +308,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
                                           typename Pr::R* smem)
 {
     using R = typename Pr::R;
+    using K = exact_t<R>;
     using TA = typename Pr::TA;
     constexpr int W = TX + 2, H = TY + 2, NT = TX * TY;
     R (*s_phi)[H][W] = reinterpret_cast<R (*)[H][W]>(smem);          // [N][H][W]
@@ -436,7 +438,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         Rx[p] = R(0);
         Ry[p] = R(0);
         mup[p] = R(0);
-        gpv[p] = R(2) * phi[p] * (R(1) - phi[p]) * (R(1) - R(2) * phi[p]);  // g'(phi), g = phi^2 (1 - phi)^2
+        gpv[p] = K(2) * phi[p] * (R(1) - phi[p]) * (R(1) - K(2) * phi[p]);  // g'(phi), g = phi^2 (1 - phi)^2
     }
 #pragma unroll
     for (int p = 0; p < N; ++p)
@@ -469,7 +471,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
             Ry[p] = rfma(a, nyv, Ry[p]);
             Rx[q] = rfma(-a, nxv, Rx[q]);
             Ry[q] = rfma(-a, nyv, Ry[q]);
-            const R gs = R(2) * s * (R(1) - s) * (R(1) - R(2) * s);
+            const R gs = K(2) * s * (R(1) - s) * (R(1) - K(2) * s);
             mup[p] += rfma(C.b2[p][q], gpv[p] - gs, C.kk[p][q] * lap[q]);
             mup[q] += rfma(C.b2[q][p], gpv[q] - gs, C.kk[q][p] * lap[p]);
         }
@@ -490,25 +492,25 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     // 1 / rho, omega_f = 1 / tau_f = rho / A and omega_h = 1 / tau_h = 1 / B from one
     // division: tau_f = A / rho, A = 3 mu + rho / 2 (tau_f = mu / (rho c_s^2) + 1/2) and
     // tau_h = B = lambda / (rho_ref c_p,ref c_s^2) + 1/2
-    const R Af = rfma(R(3), mu, R(0.5) * rho);
-    const R Bh = rfma(lam, C.tau_h_scale, R(0.5));
+    const R Af = rfma(K(3), mu, K(0.5) * rho);
+    const R Bh = rfma(lam, C.tau_h_scale, K(0.5));
     const R rAB = R(1) / (rho * Af * Bh);
     const R irho = (Af * Bh) * rAB;
     const R om = (rho * rho) * (Bh * rAB);
     const R oh = (rho * Af) * rAB;
-    const R usx = rfma(R(0.5), Fx, jx) * irho, usy = rfma(R(0.5), Fy, jy) * irho;
+    const R usx = rfma(K(0.5), Fx, jx) * irho, usy = rfma(K(0.5), Fy, jy) * irho;
     const R fpx = chi * (C.us[0] - usx), fpy = chi * (C.us[1] - usy);
-    const R ux = rfma(R(0.5), fpx, usx), uy = rfma(R(0.5), fpy, usy);
+    const R ux = rfma(K(0.5), fpx, usx), uy = rfma(K(0.5), fpy, usy);
     const R psim = (R)LBM_LDX(Pr::COH, P, ain, aux_psi() * S + c, P.aux_elems, 14);
     const R mdot = -((psi - psim) + (ux * gsx + uy * gsy)) * irho;
     const R Ssrc = rfma(rho, mdot, ux * grx + uy * gry);
-    const R Lxx = rfma(R(2) * ux, Fx, Ssrc * R(1.0 / 3.0));
-    const R Lyy = rfma(R(2) * uy, Fy, Ssrc * R(1.0 / 3.0));
+    const R Lxx = rfma(K(2) * ux, Fx, Ssrc * R(1.0 / 3.0));
+    const R Lyy = rfma(K(2) * uy, Fy, Ssrc * R(1.0 / 3.0));
     const R Lxy = rfma(ux, Fy, uy * Fx);
-    const R tmh = R(3) * mu * irho;  // tau_f - 1/2
-    const R F0 = R(wgt(0)) * rfma(R(-1.5), Lxx + Lyy, Ssrc);
+    const R tmh = K(3) * mu * irho;  // tau_f - 1/2
+    const R F0 = R(wgt(0)) * rfma(K(-1.5), Lxx + Lyy, Ssrc);
     const R uu = rfma(ux, ux, uy * uy);
-    const R p = R(0.6) * (((sum_f + R(0.5) * Ssrc) + tmh * F0) - rho * R(wgt(0)) * R(1.5) * uu);
+    const R p = R(0.6) * (((sum_f + K(0.5) * Ssrc) + tmh * F0) - rho * R(wgt(0)) * K(1.5) * uu);
 
     if (!COLLIDE) {
 #pragma unroll
@@ -526,18 +528,18 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
 
     // ---- stage F: flow collision -------------------------------------------
     {
-        const R k = rfma(R(-0.5), om, R(1)), om1 = R(1) - om;
+        const R k = rfma(K(-0.5), om, R(1)), om1 = R(1) - om;
         const R Fex = rfma(rho, fpx, Fx), Fey = rfma(rho, fpy, Fy);
         const R rom = om * rho;
-        const R a0 = om * rfma(R(-1.5) * rho, uu, R(3) * p) + k * rfma(R(-1.5), Lxx + Lyy, Ssrc);
-        const R ax = R(3) * rfma(rom, ux, k * Fex);
-        const R ay = R(3) * rfma(rom, uy, k * Fey);
-        const R axx = R(4.5) * rfma(rom * ux, ux, k * Lxx);
-        const R ayy = R(4.5) * rfma(rom * uy, uy, k * Lyy);
-        const R axy = R(9) * rfma(rom * ux, uy, k * Lxy);
+        const R a0 = om * rfma(K(-1.5) * rho, uu, K(3) * p) + k * rfma(K(-1.5), Lxx + Lyy, Ssrc);
+        const R ax = K(3) * rfma(rom, ux, k * Fex);
+        const R ay = K(3) * rfma(rom, uy, k * Fey);
+        const R axx = K(4.5) * rfma(rom * ux, ux, k * Lxx);
+        const R ayy = K(4.5) * rfma(rom * uy, uy, k * Lyy);
+        const R axy = K(9) * rfma(rom * ux, uy, k * Lxy);
         const R bx = a0 + axx, by = a0 + ayy, bd = a0 + axx + ayy;
         R X[9];
-        X[0] = rfma(R(-6.75) * om, p, a0);
+        X[0] = rfma(K(-6.75) * om, p, a0);
         X[1] = bx + ax;
         X[3] = bx - ax;
         X[2] = by + ay;
@@ -563,8 +565,8 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
             const R Dx = phi[pp] * ux - (R)LBM_LDX(Pr::COH, P, ain, aux_phiux(pp) * S + c, P.aux_elems, 15);
             const R Dy = phi[pp] * uy - (R)LBM_LDX(Pr::COH, P, ain, aux_phiuy(N, pp) * S + c, P.aux_elems, 16);
             const R b0 = og * phi[pp] + kg * phi[pp] * mdot;
-            const R bxv = R(3) * og * phi[pp] * ux + kg * rfma(R(3), Dx, Rx[pp]);
-            const R byv = R(3) * og * phi[pp] * uy + kg * rfma(R(3), Dy, Ry[pp]);
+            const R bxv = K(3) * og * phi[pp] * ux + kg * rfma(K(3), Dx, Rx[pp]);
+            const R byv = K(3) * og * phi[pp] * uy + kg * rfma(K(3), Dy, Ry[pp]);
             R q[9];
             q[0] = rfma(R(wgt(0)), b0, og1 * gq[0]);
             q[1] = rfma(R(wgt(1)), b0 + bxv, og1 * gq[1]);
@@ -587,13 +589,13 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
 #pragma unroll
         for (int i = 0; i < 9; ++i) h[i] = ld_pop_late<Pr, KIND_H>(P, pin, N + 1, i, c, 7);
         const R Z = rho * cp * T, E = C.E_ref * T;
-        const R kh = rfma(R(-0.5), oh, R(1)), oh1 = R(1) - oh;
+        const R kh = rfma(K(-0.5), oh, R(1)), oh1 = R(1) - oh;
         const R Zm = Z * mdot;
-        const R c0 = oh * rfma(R(-1.5) * Z, uu, E) + kh * Zm;
+        const R c0 = oh * rfma(K(-1.5) * Z, uu, E) + kh * Zm;
         const R ohZ = oh * Z;
-        const R cxv = R(3) * ohZ * ux, cyv = R(3) * ohZ * uy;
-        const R cxx = R(4.5) * ohZ * ux * ux, cyy = R(4.5) * ohZ * uy * uy, cxy = R(9) * ohZ * ux * uy;
-        const R heq0 = (rhoH - E) + R(wgt(0)) * rfma(R(-1.5) * Z, uu, E);
+        const R cxv = K(3) * ohZ * ux, cyv = K(3) * ohZ * uy;
+        const R cxx = K(4.5) * ohZ * ux * ux, cyy = K(4.5) * ohZ * uy * uy, cxy = K(9) * ohZ * ux * uy;
+        const R heq0 = (rhoH - E) + R(wgt(0)) * rfma(K(-1.5) * Z, uu, E);
         const R bx = c0 + cxx, by = c0 + cyy, bd = c0 + cxx + cyy;
         R q[9];
         q[0] = rfma(oh, heq0, rfma(kh * R(wgt(0)), Zm, oh1 * h[0]));
@@ -618,9 +620,9 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         if (dside >= 0) {
             const bool top = dside == 3;
             const R vy = top ? -uy : uy;
-            const R Eg = C.E_ref * (R(2) * C.Tw[dside] - T);
+            const R Eg = C.E_ref * (K(2) * C.Tw[dside] - T);
             // equilibrium of a moving direction with weight w and c_j . u = cu
-            auto heq = [&](R w, R cu) { return w * rfma(Z, rfma(R(4.5) * cu, cu, rfma(R(3), cu, R(-1.5) * uu)), E); };
+            auto heq = [&](R w, R cu) { return w * rfma(Z, rfma(K(4.5) * cu, cu, rfma(K(3), cu, K(-1.5) * uu)), E); };
             const R wa = R(wgt(2)), wd = R(wgt(5));
             push_row_at<KIND_H, Pr>(P, pout, N + 1, top ? 4 : 2, 0, x, y,
                                     rfma(oh1, (top ? h[4] : h[2]) - heq(wa, vy), wa * Eg));
