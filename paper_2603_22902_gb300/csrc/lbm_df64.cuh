@@ -69,8 +69,8 @@ __device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
 // SloppyDWPlusDW: the exact sum of the high words, then the low words added with one
 // rounding.  Its error is at most ~3u^2 (|x| + |y|): relative to the operands, not to
 // the result, which is what an absolute tolerance on the fields needs.  (The accurate
-// variant, relative to the result, costs 9 more instructions per sum and changed no
-// field of the parity cases by more than 1e-12.)
+// variant, relative to the result, costs 9 more instructions per sum; on the parity
+// cases it lowered the largest error of any field by 3 % at most.)
 __device__ __forceinline__ df64 operator+(df64 x, df64 y)
 {
     const df64 s = dw_2sum(x.hi, y.hi);

@@ -104,7 +104,7 @@ struct PrecDF64 {
     static constexpr bool QUANT = false;
     static constexpr double NABS2 = 1e-24;
     static constexpr float NGUARD = 0.0f;
-    static constexpr int OCC_THREADS = 512;
+    static constexpr int OCC_THREADS = 768;
     static constexpr bool COH = false;
     static constexpr bool COMPACT = true;
 };

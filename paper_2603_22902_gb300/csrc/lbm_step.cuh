@@ -508,9 +508,9 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     const R Lyy = rfma(K(2) * uy, Fy, Ssrc * R(1.0 / 3.0));
     const R Lxy = rfma(ux, Fy, uy * Fx);
     const R tmh = K(3) * mu * irho;  // tau_f - 1/2
-    const R F0 = R(wgt(0)) * rfma(K(-1.5), Lxx + Lyy, Ssrc);
+    const R F0 = wgt_r<R>(0) * rfma(K(-1.5), Lxx + Lyy, Ssrc);
     const R uu = rfma(ux, ux, uy * uy);
-    const R p = R(0.6) * (((sum_f + K(0.5) * Ssrc) + tmh * F0) - rho * R(wgt(0)) * K(1.5) * uu);
+    const R p = R(0.6) * (((sum_f + K(0.5) * Ssrc) + tmh * F0) - rho * wgt_r<R>(0) * K(1.5) * uu);
 
     if (!COLLIDE) {
 #pragma unroll
@@ -550,7 +550,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         X[8] = (bd - axy) - (ay - ax);
         R q[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) q[i] = rfma(R(wgt(i)), X[i], om1 * f[i]);
+        for (int i = 0; i < 9; ++i) q[i] = rfma(wgt_r<R>(i), X[i], om1 * f[i]);
         push_species<KIND_F, Pr>(P, pout, 0, x, y, q);
     }
 
@@ -568,15 +568,15 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
             const R bxv = K(3) * og * phi[pp] * ux + kg * rfma(K(3), Dx, Rx[pp]);
             const R byv = K(3) * og * phi[pp] * uy + kg * rfma(K(3), Dy, Ry[pp]);
             R q[9];
-            q[0] = rfma(R(wgt(0)), b0, og1 * gq[0]);
-            q[1] = rfma(R(wgt(1)), b0 + bxv, og1 * gq[1]);
-            q[3] = rfma(R(wgt(3)), b0 - bxv, og1 * gq[3]);
-            q[2] = rfma(R(wgt(2)), b0 + byv, og1 * gq[2]);
-            q[4] = rfma(R(wgt(4)), b0 - byv, og1 * gq[4]);
-            q[5] = rfma(R(wgt(5)), b0 + (bxv + byv), og1 * gq[5]);
-            q[7] = rfma(R(wgt(7)), b0 - (bxv + byv), og1 * gq[7]);
-            q[6] = rfma(R(wgt(6)), b0 + (byv - bxv), og1 * gq[6]);
-            q[8] = rfma(R(wgt(8)), b0 - (byv - bxv), og1 * gq[8]);
+            q[0] = rfma(wgt_r<R>(0), b0, og1 * gq[0]);
+            q[1] = rfma(wgt_r<R>(1), b0 + bxv, og1 * gq[1]);
+            q[3] = rfma(wgt_r<R>(3), b0 - bxv, og1 * gq[3]);
+            q[2] = rfma(wgt_r<R>(2), b0 + byv, og1 * gq[2]);
+            q[4] = rfma(wgt_r<R>(4), b0 - byv, og1 * gq[4]);
+            q[5] = rfma(wgt_r<R>(5), b0 + (bxv + byv), og1 * gq[5]);
+            q[7] = rfma(wgt_r<R>(7), b0 - (bxv + byv), og1 * gq[7]);
+            q[6] = rfma(wgt_r<R>(6), b0 + (byv - bxv), og1 * gq[6]);
+            q[8] = rfma(wgt_r<R>(8), b0 - (byv - bxv), og1 * gq[8]);
             push_species<KIND_G, Pr>(P, pout, 1 + pp, x, y, q);
             LBM_ST(P, aout, aux_phiux(pp) * S + c, P.aux_elems, 30, (TA)(phi[pp] * ux));
             LBM_ST(P, aout, aux_phiuy(N, pp) * S + c, P.aux_elems, 31, (TA)(phi[pp] * uy));
@@ -595,18 +595,18 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         const R ohZ = oh * Z;
         const R cxv = K(3) * ohZ * ux, cyv = K(3) * ohZ * uy;
         const R cxx = K(4.5) * ohZ * ux * ux, cyy = K(4.5) * ohZ * uy * uy, cxy = K(9) * ohZ * ux * uy;
-        const R heq0 = (rhoH - E) + R(wgt(0)) * rfma(K(-1.5) * Z, uu, E);
+        const R heq0 = (rhoH - E) + wgt_r<R>(0) * rfma(K(-1.5) * Z, uu, E);
         const R bx = c0 + cxx, by = c0 + cyy, bd = c0 + cxx + cyy;
         R q[9];
-        q[0] = rfma(oh, heq0, rfma(kh * R(wgt(0)), Zm, oh1 * h[0]));
-        q[1] = rfma(R(wgt(1)), bx + cxv, oh1 * h[1]);
-        q[3] = rfma(R(wgt(3)), bx - cxv, oh1 * h[3]);
-        q[2] = rfma(R(wgt(2)), by + cyv, oh1 * h[2]);
-        q[4] = rfma(R(wgt(4)), by - cyv, oh1 * h[4]);
-        q[5] = rfma(R(wgt(5)), (bd + cxy) + (cxv + cyv), oh1 * h[5]);
-        q[7] = rfma(R(wgt(7)), (bd + cxy) - (cxv + cyv), oh1 * h[7]);
-        q[6] = rfma(R(wgt(6)), (bd - cxy) + (cyv - cxv), oh1 * h[6]);
-        q[8] = rfma(R(wgt(8)), (bd - cxy) - (cyv - cxv), oh1 * h[8]);
+        q[0] = rfma(oh, heq0, rfma(kh * wgt_r<R>(0), Zm, oh1 * h[0]));
+        q[1] = rfma(wgt_r<R>(1), bx + cxv, oh1 * h[1]);
+        q[3] = rfma(wgt_r<R>(3), bx - cxv, oh1 * h[3]);
+        q[2] = rfma(wgt_r<R>(2), by + cyv, oh1 * h[2]);
+        q[4] = rfma(wgt_r<R>(4), by - cyv, oh1 * h[4]);
+        q[5] = rfma(wgt_r<R>(5), (bd + cxy) + (cxv + cyv), oh1 * h[5]);
+        q[7] = rfma(wgt_r<R>(7), (bd + cxy) - (cxv + cyv), oh1 * h[7]);
+        q[6] = rfma(wgt_r<R>(6), (bd - cxy) + (cyv - cxv), oh1 * h[6]);
+        q[8] = rfma(wgt_r<R>(8), (bd - cxy) - (cyv - cxv), oh1 * h[8]);
         // outflow rows are copied inside push_species; Dirichlet rows get their
         // incoming populations from the ghost rule below
         push_species<KIND_H, Pr>(P, pout, N + 1, x, y, q);
@@ -623,7 +623,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
             const R Eg = C.E_ref * (K(2) * C.Tw[dside] - T);
             // equilibrium of a moving direction with weight w and c_j . u = cu
             auto heq = [&](R w, R cu) { return w * rfma(Z, rfma(K(4.5) * cu, cu, rfma(K(3), cu, K(-1.5) * uu)), E); };
-            const R wa = R(wgt(2)), wd = R(wgt(5));
+            const R wa = wgt_r<R>(2), wd = wgt_r<R>(5);
             push_row_at<KIND_H, Pr>(P, pout, N + 1, top ? 4 : 2, 0, x, y,
                                     rfma(oh1, (top ? h[4] : h[2]) - heq(wa, vy), wa * Eg));
             push_row_at<KIND_H, Pr>(P, pout, N + 1, top ? 8 : 5, 1, x, y,
