@@ -78,7 +78,7 @@ batch_persistent_kernel(const BatchTable T, int nsteps)
     using PC = Coherent<Pr>;
     using TA = typename Pr::TA;
     __shared__ KParams sP;
-    __shared__ typename Pr::R smem[tile_smem_elems<N, TX, TY>()];
+    __shared__ typename Pr::R smem[tile_smem_elems<N, TX, TY, Pr>()];
     const int a0 = *(volatile unsigned char*)T.parity;
     int loaded = -1;
     for (int s = 0; s < nsteps; ++s) {
@@ -110,7 +110,7 @@ batch_step_kernel(const BatchTable T, int s)
     static_assert(TX * TY == BATCH_NT, "batch tiles have BATCH_NT cells");
     using TA = typename Pr::TA;
     __shared__ KParams sP;
-    __shared__ typename Pr::R smem[tile_smem_elems<N, TX, TY>()];
+    __shared__ typename Pr::R smem[tile_smem_elems<N, TX, TY, Pr>()];
     const int t = blockIdx.x;
     const int c = __ldg(T.tile_case + t);
     load_params(sP, T.params + c);

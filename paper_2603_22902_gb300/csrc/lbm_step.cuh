@@ -290,15 +290,15 @@ __device__ __forceinline__ void push_species(const KParams& P, const PopView<Pr>
 #define LBM_OCC(Pr) (Pr::OCC_THREADS)
 #endif
 // Shared-memory elements of type R that step_tile needs: phi_p, rho and psi on the
-// tile and its one-cell ring, and rho H, f_l, T of the tile's cells.
-template <int N, int TX, int TY>
+// tile and its one-cell ring, and (COMPACT policies) rho H, f_l, T of the tile's cells.
+template <int N, int TX, int TY, class Pr>
 __host__ __device__ constexpr int tile_smem_elems()
 {
-    return (N + 2) * (TX + 2) * (TY + 2) + 3 * TX * TY;
+    return (N + 2) * (TX + 2) * (TY + 2) + (Pr::COMPACT ? 3 * TX * TY : 0);
 }
 
 // One TX x TY tile (tile column bx, row by) of one time step, run by a block of
-// TX * TY threads; smem holds tile_smem_elems<N, TX, TY>() elements of shared memory.
+// TX * TY threads; smem holds tile_smem_elems<N, TX, TY, Pr>() elements of shared memory.
 // Every thread of the block must call it (it holds two block barriers); the caller
 // places a block barrier before smem is used again.
 template <int N, int TX, int TY, bool COLLIDE, class Pr>
@@ -314,7 +314,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     R (*s_phi)[H][W] = reinterpret_cast<R (*)[H][W]>(smem);          // [N][H][W]
     R (*s_rho)[W] = reinterpret_cast<R (*)[W]>(smem + N * H * W);    // [H][W]
     R (*s_psi)[W] = reinterpret_cast<R (*)[W]>(smem + (N + 1) * H * W);
-    R (*s_own)[NT] = reinterpret_cast<R (*)[NT]>(smem + (N + 2) * H * W);  // rho H, f_l, T of the own cells
+    R (*s_own)[NT] = reinterpret_cast<R (*)[NT]>(smem + (N + 2) * H * W);  // COMPACT: rho H, f_l, T of own cells
 
     const int nx = P.nx, ny = P.ny;
     const long long S = P.S;
@@ -327,15 +327,12 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     const PopView<Pr> pin = pop_view<Pr>(P, pin_base);
     const Coef<R>& C = coef<R>(P);
 
-    // ---- stages A + B on the tile and its one-cell ring ----------------------
-    // One code path for all (TX + 2)(TY + 2) positions, so the moments are compiled once.
-    // The cell coordinates are brought into range before anything else (periodic: full
-    // modulo, since a tile may be wider / taller than the domain; otherwise: clamped and
-    // skipped), so no address outside the planes is ever formed, even for a position
-    // whose value the ghost rule supplies later.
-#pragma unroll 1
-    for (int k = tid; k < W * H; k += NT) {
-        const int lx = k % W, ly = k / W;
+    // Position (lx, ly) of the tile-with-ring as a cell of the lattice.  The coordinates
+    // are brought into range before anything else (periodic: full modulo, since a tile may
+    // be wider / taller than the domain; otherwise clamped, and the position is reported as
+    // beyond the domain, to be filled by the ghost rule), so no address outside the planes
+    // is ever formed.
+    auto locate = [&](int lx, int ly, long long& cell) {
         int gx = x0 + lx - 1, gy = y0 + ly - 1;
         bool beyond = false;
         if (gx < 0 || gx >= nx) {
@@ -346,20 +343,67 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
             if (yper) gy = wrap_index(gy, ny);
             else { beyond = true; gy = min(max(gy, 0), ny - 1); }
         }
-        if (beyond) continue;
-        const int ox = lx - 1, oy = ly - 1;
-        const bool own = (unsigned)ox < (unsigned)TX && (unsigned)oy < (unsigned)TY;
-        R ph[N], rH, flv, Tv, r, ps;
-        cell_moments<N, Pr>(P, pin, ain, (long long)gy * nx + gx, ph, rH, flv, Tv, r, ps);
+        cell = (long long)gy * nx + gx;
+        return !beyond;
+    };
+    R phi[N], rhoH, fl, T, rho, psi, mu, lam, cp, chi;
+    if constexpr (Pr::COMPACT) {
+        // ---- stages A + B: one code path for all (TX + 2)(TY + 2) positions, so that
+        // the moments are compiled once; the own cells' rho H, f_l, T go to shared memory
+#pragma unroll 1
+        for (int k = tid; k < W * H; k += NT) {
+            const int lx = k % W, ly = k / W;
+            long long cell;
+            if (!locate(lx, ly, cell)) continue;
+            R ph[N], rH, flv, Tv, r, ps;
+            cell_moments<N, Pr>(P, pin, ain, cell, ph, rH, flv, Tv, r, ps);
 #pragma unroll
-        for (int p = 0; p < N; ++p) s_phi[p][ly][lx] = ph[p];
-        s_rho[ly][lx] = r;
-        s_psi[ly][lx] = ps;
-        if (own) {
-            const int o = oy * TX + ox;
-            s_own[0][o] = rH;
-            s_own[1][o] = flv;
-            s_own[2][o] = Tv;
+            for (int p = 0; p < N; ++p) s_phi[p][ly][lx] = ph[p];
+            s_rho[ly][lx] = r;
+            s_psi[ly][lx] = ps;
+            const int ox = lx - 1, oy = ly - 1;
+            if ((unsigned)ox < (unsigned)TX && (unsigned)oy < (unsigned)TY) {
+                const int o = oy * TX + ox;
+                s_own[0][o] = rH;
+                s_own[1][o] = flv;
+                s_own[2][o] = Tv;
+            }
+        }
+    } else {
+        // ---- stages A + B: the own cell in registers (the rest of eq. 2 as well),
+        // then the ring, phi_p, rho and psi only -----------------------------------
+        auto halo_at = [&](int lx, int ly) {
+            long long cell;
+            if (!locate(lx, ly, cell)) return;
+            R ph[N], r, ps;
+            halo_moments<N, Pr>(P, pin, ain, cell, ph, r, ps);
+#pragma unroll
+            for (int p = 0; p < N; ++p) s_phi[p][ly][lx] = ph[p];
+            s_rho[ly][lx] = r;
+            s_psi[ly][lx] = ps;
+        };
+        if (owned) {
+            cell_moments<N, Pr>(P, pin, ain, (long long)y * nx + x, phi, rhoH, fl, T, rho, psi);
+            const R fs = R(1) - fl;
+            mu = rfma(fs, mix_sum<N, R>(phi, C.mu_s), fl * mix_sum<N, R>(phi, C.mu_l));
+            lam = rfma(fs, mix_sum<N, R>(phi, C.lam_s), fl * mix_sum<N, R>(phi, C.lam_l));
+            cp = rfma(fs, mix_sum<N, R>(phi, C.cp_s), fl * mix_sum<N, R>(phi, C.cp_l));
+            chi = fs * mix_sum<N, R>(phi, C.pcm);
+#pragma unroll
+            for (int p = 0; p < N; ++p) s_phi[p][ty + 1][tx + 1] = phi[p];
+            s_rho[ty + 1][tx + 1] = rho;
+            s_psi[ty + 1][tx + 1] = psi;
+        } else {
+            halo_at(tx + 1, ty + 1);
+        }
+        constexpr int NRING = 2 * W + 2 * TY;
+        for (int k = tid; k < NRING; k += NT) {
+            int lx, ly;
+            if (k < W) { lx = k; ly = 0; }
+            else if (k < 2 * W) { lx = k - W; ly = H - 1; }
+            else if (k < 2 * W + TY) { lx = 0; ly = k - 2 * W + 1; }
+            else { lx = W - 1; ly = k - 2 * W - TY + 1; }
+            halo_at(lx, ly);
         }
     }
     __syncthreads();
@@ -396,19 +440,23 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     __syncthreads();
     if (!owned) return;
 
-    // ---- own cell: the rest of eq. 2 -------------------------------------------
     const int lx = tx + 1, ly = ty + 1;
     const long long c = (long long)y * nx + x;
-    R phi[N];
+    if constexpr (Pr::COMPACT) {
+        // ---- own cell: the rest of eq. 2 ---------------------------------------
 #pragma unroll
-    for (int p = 0; p < N; ++p) phi[p] = s_phi[p][ly][lx];
-    const R rhoH = s_own[0][tid], fl = s_own[1][tid], T = s_own[2][tid];
-    const R rho = s_rho[ly][lx], psi = s_psi[ly][lx];
-    const R fs = R(1) - fl;
-    const R mu = rfma(fs, mix_sum<N, R>(phi, C.mu_s), fl * mix_sum<N, R>(phi, C.mu_l));
-    const R lam = rfma(fs, mix_sum<N, R>(phi, C.lam_s), fl * mix_sum<N, R>(phi, C.lam_l));
-    const R cp = rfma(fs, mix_sum<N, R>(phi, C.cp_s), fl * mix_sum<N, R>(phi, C.cp_l));
-    const R chi = fs * mix_sum<N, R>(phi, C.pcm);
+        for (int p = 0; p < N; ++p) phi[p] = s_phi[p][ly][lx];
+        rhoH = s_own[0][tid];
+        fl = s_own[1][tid];
+        T = s_own[2][tid];
+        rho = s_rho[ly][lx];
+        psi = s_psi[ly][lx];
+        const R fs = R(1) - fl;
+        mu = rfma(fs, mix_sum<N, R>(phi, C.mu_s), fl * mix_sum<N, R>(phi, C.mu_l));
+        lam = rfma(fs, mix_sum<N, R>(phi, C.lam_s), fl * mix_sum<N, R>(phi, C.lam_l));
+        cp = rfma(fs, mix_sum<N, R>(phi, C.cp_s), fl * mix_sum<N, R>(phi, C.cp_l));
+        chi = fs * mix_sum<N, R>(phi, C.pcm);
+    }
 
     // ---- stage C: isotropic stencils ---------------------------------------
     R gpx[N], gpy[N], lap[N];
@@ -645,7 +693,7 @@ __global__ void __launch_bounds__(TX * TY, (LBM_OCC(Pr) + TX * TY - 1) / (TX * T
 fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __restrict__ pout_base,
                   const typename Pr::TA* __restrict__ ain, typename Pr::TA* __restrict__ aout, ExportPtrs ex)
 {
-    __shared__ typename Pr::R smem[tile_smem_elems<N, TX, TY>()];
+    __shared__ typename Pr::R smem[tile_smem_elems<N, TX, TY, Pr>()];
     step_tile<N, TX, TY, COLLIDE, Pr>(P, pin_base, pout_base, ain, aout, ex, blockIdx.x, blockIdx.y, smem);
 }
 
