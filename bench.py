@@ -54,16 +54,22 @@ def bytes_per_lu(N: int, precision: str = "fp64") -> int:
 # of that pipe: 152 SMs x 2 FP64 lanes per clock x 2.07 GHz = 629.3 G thread-instructions
 # per second (x 2 flop per FMA = 1.259 TFLOP/s).
 FP64_PIPE_PEAK_GINST = 152 * 2 * 2.070
+# Instruction issue: 152 SMs x 4 schedulers x 1 warp-instruction per clock x 2.07 GHz.
+# The double-word step runs ~4500 FP32 instructions per lattice update on the FP32 pipes
+# and is bound by this issue rate rather than by any one pipe or by HBM.
+ISSUE_PEAK_GWINST = 152 * 4 * 2.070
 # Per lattice update of the fused step kernel, from one ncu capture of the kernel built
 # from the sources with digest `digest` (sessile drop 512^2, N = 2, 32 x 8 tiles):
-# FP64-pipe thread-instructions, FP64 flop (DFMA = 2, DADD / DMUL = 1) and DRAM bytes.
+# FP64-pipe thread-instructions, FP64 flop (DFMA = 2, DADD / DMUL = 1), warp-instructions
+# issued, FP32 thread-instructions (FADD + FMUL + FFMA) and DRAM bytes.
 # A changed kernel has another digest, and then these counts are not reported.
 # (DRAM bytes are what ncu saw during the launch: part of the writes of a launch is
 # still in L2 when it ends and reaches DRAM during the next one.)
-_D = "8f1297efaba9edc5b46d5d6e210e1b164fdb854fe655746906d6e509c56257a2"
+_D = "ff1523819ff8176cc1d20a1a7bd79929e3614b1568a31c1ab1938be4f4dd402e"
 NCU_COUNTS = {
-    ("fp64", 2): {"digest": _D, "fp64_inst": 491.7, "fp64_flop": 666.8, "dram_bytes": 508.4},
-    ("fp16s", 2): {"digest": _D, "fp64_inst": 36.5, "fp64_flop": 50.1, "dram_bytes": 108.7},
+    ("fp64", 2): {"digest": _D, "fp64_inst": 487.0, "fp64_flop": 660.9, "warp_inst": 114.8, "dram_bytes": 520.5},
+    ("df64", 2): {"digest": _D, "fp64_inst": 59.6, "warp_inst": 199.6, "fp32_inst": 4502.1, "dram_bytes": 550.8},
+    ("fp16s", 2): {"digest": _D, "fp64_inst": 36.5, "fp64_flop": 50.1, "warp_inst": 70.2, "dram_bytes": 108.5},
 }
 
 
@@ -386,6 +392,19 @@ def compare_precision(case, precisions, mlups_fp64, front_steps, stream, flush):
         if front_steps > 0:
             r.update({"front_steps": front_steps, "front_fp64_lu": round(fronts["fp64"], 4),
                       "front_err_lu": float(f"{abs(fronts[prec] - fronts['fp64']):.3g}"), "front_err_bound_lu": 0.5})
+        counts = ncu_counts(prec, case.N)
+        if counts:
+            wi = counts["warp_inst"] * mlups * 1e6 / 1e9
+            r["issue"] = {"achieved": round(wi, 1), "peak": round(ISSUE_PEAK_GWINST, 1), "unit": "G warp-inst/s",
+                          "frac": round(wi / ISSUE_PEAK_GWINST, 4), "warp_inst_per_lu": counts["warp_inst"],
+                          "peak_kind": "derived: 152 SMs x 4 schedulers x 1 warp-inst/clock x 2.07 GHz"}
+            fi = counts["fp64_inst"] * mlups * 1e6 / 1e9
+            r["fp64_pipe"] = {"achieved": round(fi, 1), "peak": round(FP64_PIPE_PEAK_GINST, 1),
+                              "unit": "G FP64-pipe inst/s", "frac": round(fi / FP64_PIPE_PEAK_GINST, 4),
+                              "fp64_inst_per_lu": counts["fp64_inst"]}
+            if "fp32_inst" in counts:
+                r["issue"]["fp32_inst_per_lu"] = counts["fp32_inst"]
+            r["traffic"] = round(counts["dram_bytes"] * case.cells)
         out[prec] = r
     return out
 
