@@ -156,6 +156,7 @@ int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_t
         P.d.cp_l[p] = ph.cp_l;
         P.d.cp_s[p] = ph.cp_s;
         P.rhoL[p] = ph.rho_l * ph.latent;
+        P.d.rhoL[p] = P.rhoL[p];
         P.d.drho[p] = ph.rho_s - ph.rho_l;
         P.d.pcm[p] = ph.latent > 0.0 ? 1.0 : 0.0;
         for (int q = 0; q < N; ++q) {
@@ -167,8 +168,8 @@ int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_t
         }
     }
     P.d.four_eps = 4.0 / num->eps;
-    P.T_sol = th->T_sol;
-    P.T_liq = th->T_liq;
+    P.T_sol = P.d.T_sol = th->T_sol;
+    P.T_liq = P.d.T_liq = th->T_liq;
     const double cp_ref = th->cp_ref > 0.0 ? th->cp_ref
                                            : 2.0 * phases[0].cp_s * phases[0].cp_l / (phases[0].cp_s + phases[0].cp_l);
     P.d.E_ref = th->rho_ref * cp_ref;

@@ -69,6 +69,8 @@ struct Coef {
     T us[2], accel[2];
     T omega_g, kg;                // 1 / tau_g and 1 - 1/(2 tau_g), tau_g = M / c_s^2 + 1/2
     T Tw[4];                      // Dirichlet wall temperature
+    T rhoL[MAXN];                 // rho_l^p L_p (the FP64 map reads KParams::rhoL)
+    T T_sol, T_liq;               // (the FP64 map reads KParams::T_sol, T_liq)
 };
 
 // Parameter block passed by value to every kernel (lives in the constant bank).

@@ -125,6 +125,54 @@ __device__ __forceinline__ void st_pop(const KParams& P, const PopView<Pr>& v, i
     }
 }
 
+// eq. H for one cell: f_l (and T when WANT_T) from rho H and phi_p, in FP64.  Policies
+// that compute in FP32 screen the cell in FP32 first: where rho H lies above the
+// liquidus value Al, or (with phase-changing material present) below the solidus value
+// As, by more than 1e-5 of the magnitudes involved (25 times the FP32 rounding bound of
+// As and Al), the FP64 map would return f_l = 1 or 0 as well, and T is then taken from
+// the same branch formula in FP32.  Only the other cells (the mushy band, values near a
+// threshold, phase-changing material below FP32 range) run the FP64 map, so f_l is the
+// FP64 map's value in every cell.
+template <int N, class Pr, bool WANT_T>
+__device__ __forceinline__ void map_cell(const KParams& P, const typename Pr::R (&phi)[N], typename Pr::R rhoH,
+                                         typename Pr::R& fl, typename Pr::R& T)
+{
+    using R = typename Pr::R;
+    if constexpr (std::is_same<R, float>::value) {
+        const Coef<float>& C = P.f;
+        float rs = 0.0f, rl = 0.0f, cs = 0.0f, cl = 0.0f, Lv = 0.0f;
+#pragma unroll
+        for (int p = 0; p < N; ++p) {
+            rs = fmaf(phi[p], C.rho_s[p], rs);
+            rl = fmaf(phi[p], C.rho_l[p], rl);
+            cs = fmaf(phi[p], C.cp_s[p], cs);
+            cl = fmaf(phi[p], C.cp_l[p], cl);
+            Lv = fmaf(phi[p], C.rhoL[p], Lv);
+        }
+        const float rcs = rs * cs, rcl = rl * cl;
+        const float As = rcs * C.T_sol, Al = fmaf(rcl, C.T_liq, Lv);
+        const float tol = 1e-5f * (fabsf(As) + fabsf(rcl * C.T_liq) + fabsf(Lv) + fabsf(rhoH)) + 1e-30f;
+        if (rhoH > Al + tol) {
+            fl = 1.0f;
+            if (WANT_T) T = C.T_liq + (rhoH - Al) / rcl;
+            return;
+        }
+        if (Lv > 0.0f && rhoH < As - tol) {
+            fl = 0.0f;
+            if (WANT_T) T = rhoH / rcs;
+            return;
+        }
+    }
+    double phd[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) phd[p] = (double)phi[p];
+    const Mix<N> m = mixture_map<N>(P, phd);
+    double fld, Td = 0.0;
+    enthalpy_map<N, WANT_T>(P, m, (double)rhoH, fld, Td);
+    fl = (R)fld;
+    if (WANT_T) T = (R)Td;
+}
+
 // Stage A + B for a halo cell: phi_p, rho and psi only (the map in FP64).
 template <int N, class Pr>
 __device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>& pin,
@@ -136,31 +184,28 @@ __device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>
     const R mdm = (R)LBM_LDX(Pr::COH, P, ain, aux_mdot() * S + c, P.aux_elems, 1);
     const R Qm = (R)LBM_LDX(Pr::COH, P, ain, aux_Q() * S + c, P.aux_elems, 2);
     const R iden = R(1) / (R(1) - R(0.5) * mdm);
-    double phd[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) {
         R s = R(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) s += ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 3);
         phi[p] = s * iden;
-        phd[p] = (double)phi[p];
     }
     R sh = R(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 4);
-    const double rhoH = (double)rfma(R(0.5), Qm, sh);
-    // eq. H in FP64; the rest of eq. 2 in R
-    const Mix<N> m = mixture_map<N>(P, phd);
-    double fld, T;
-    enthalpy_map<N, false>(P, m, rhoH, fld, T);
+    const R rhoH = rfma(R(0.5), Qm, sh);
+    // eq. H (f_l as the FP64 map gives it); the rest of eq. 2 in R
+    R fl, T;
+    map_cell<N, Pr, false>(P, phi, rhoH, fl, T);
     const Coef<R>& C = coef<R>(P);
-    const R fl = (R)fld, fs = R(1) - fl;
+    const R fs = R(1) - fl;
     rho = rfma(fs, mix_sum<N, R>(phi, C.rho_s), fl * mix_sum<N, R>(phi, C.rho_l));
     psi = fs * mix_sum<N, R>(phi, C.drho);
 }
 
 // Stage A + B of one cell of the tile or its ring: phi_p, rho H, f_l, T, rho and psi.
-// The map runs in FP64, the rest of eq. 2 in R.  T is needed only for the tile's own
+// f_l is the FP64 map's (map_cell), the rest of eq. 2 runs in R.  T is needed only for the tile's own
 // cells, but almost every warp holds both kinds, so it is computed for all (a branch on
 // the kind would run both versions of the map).
 template <int N, class Pr>
@@ -175,25 +220,19 @@ __device__ __forceinline__ void cell_moments(const KParams& P, const PopView<Pr>
     const R mdm = (R)LBM_LDX(Pr::COH, P, ain, aux_mdot() * S + c, P.aux_elems, 1);
     const R Qm = (R)LBM_LDX(Pr::COH, P, ain, aux_Q() * S + c, P.aux_elems, 2);
     const R iden = R(1) / (R(1) - K(0.5) * mdm);
-    double phd[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) {
         R s = R(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) s += ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 3);
         phi[p] = s * iden;
-        phd[p] = (double)phi[p];
     }
     R sh = R(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 4);
     rhoH = rfma(K(0.5), Qm, sh);
-    const Mix<N> m = mixture_map<N>(P, phd);
-    double fld, Td;
-    enthalpy_map<N, true>(P, m, (double)rhoH, fld, Td);
+    map_cell<N, Pr, true>(P, phi, rhoH, fl, T);
     const Coef<R>& C = coef<R>(P);
-    fl = (R)fld;
-    T = (R)Td;
     const R fs = R(1) - fl;
     rho = rfma(fs, mix_sum<N, R>(phi, C.rho_s), fl * mix_sum<N, R>(phi, C.rho_l));
     psi = fs * mix_sum<N, R>(phi, C.drho);
