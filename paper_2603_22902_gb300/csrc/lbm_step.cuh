@@ -498,25 +498,24 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     }
 
     // ---- stage C: isotropic stencils ---------------------------------------
-    R gpx[N], gpy[N], lap[N];
-    auto grad = [&](R (*a)[W], R& gx_, R& gy_) {
+    // gradients of phi_p (fields 0..N-1), rho (N) and psi (N+1), Laplacians of phi_p; the
+    // fields are consecutive planes of shared memory (one rolled loop in COMPACT builds)
+    R gpx[N + 2], gpy[N + 2], lap[N];
+#pragma unroll(Pr::COMPACT ? 1 : N + 2)
+    for (int fi = 0; fi < N + 2; ++fi) {
+        R (*a)[W] = reinterpret_cast<R (*)[W]>(smem + fi * H * W);
         const R e = a[ly][lx + 1], w = a[ly][lx - 1], n = a[ly + 1][lx], s = a[ly - 1][lx];
         const R ne = a[ly + 1][lx + 1], nw = a[ly + 1][lx - 1], se = a[ly - 1][lx + 1], sw = a[ly - 1][lx - 1];
-        gx_ = (e - w) * R(1.0 / 3.0) + ((ne - nw) + (se - sw)) * R(1.0 / 12.0);
-        gy_ = (n - s) * R(1.0 / 3.0) + ((ne - se) + (nw - sw)) * R(1.0 / 12.0);
-    };
-#pragma unroll
-    for (int p = 0; p < N; ++p) {
-        R (*a)[W] = s_phi[p];
-        grad(a, gpx[p], gpy[p]);
-        const R v0 = a[ly][lx];
-        const R ax = (a[ly][lx + 1] + a[ly][lx - 1]) + (a[ly + 1][lx] + a[ly - 1][lx]);
-        const R dg = (a[ly + 1][lx + 1] + a[ly + 1][lx - 1]) + (a[ly - 1][lx + 1] + a[ly - 1][lx - 1]);
-        lap[p] = ax * R(2.0 / 3.0) + dg * R(1.0 / 6.0) - v0 * R(10.0 / 3.0);
+        gpx[fi] = (e - w) * R(1.0 / 3.0) + ((ne - nw) + (se - sw)) * R(1.0 / 12.0);
+        gpy[fi] = (n - s) * R(1.0 / 3.0) + ((ne - se) + (nw - sw)) * R(1.0 / 12.0);
+        if (fi < N) {
+            const R v0 = a[ly][lx];
+            const R ax = (e + w) + (n + s);
+            const R dg = (ne + nw) + (se + sw);
+            lap[fi] = ax * R(2.0 / 3.0) + dg * R(1.0 / 6.0) - v0 * R(10.0 / 3.0);
+        }
     }
-    R grx, gry, gsx, gsy;
-    grad(s_rho, grx, gry);
-    grad(s_psi, gsx, gsy);
+    const R grx = gpx[N], gry = gpy[N], gsx = gpx[N + 1], gsy = gpy[N + 1];
 
     // ---- stage D: pairwise normals, R_p, chemical potentials, F_s -----------
     R Rx[N], Ry[N], mup[N], gpv[N];
