@@ -694,6 +694,8 @@ __global__ void __launch_bounds__(128) adj_cell_kernel(const KParams P, const Ad
             for (int f2 = 0; f2 < N + 2; ++f2) sb[k][f2] = 0.0;
         // point adjoints before folding: vb[k][field]
         double vb[9][N + 2];
+        for (int k = 0; k < 9; ++k)
+            for (int f2 = 0; f2 < N + 2; ++f2) vb[k][f2] = 0.0;
         auto grad_rev = [&](int fld, double gx_b, double gy_b) {
             vb[1][fld] += gx_b * (1.0 / 3.0);
             vb[3][fld] -= gx_b * (1.0 / 3.0);
@@ -704,8 +706,6 @@ __global__ void __launch_bounds__(128) adj_cell_kernel(const KParams P, const Ad
             vb[2][fld] += gy_b * (1.0 / 3.0);
             vb[4][fld] -= gy_b * (1.0 / 3.0);
         };
-        for (int k = 0; k < 9; ++k)
-            for (int f2 = 0; f2 < N + 2; ++f2) vb[k][f2] = 0.0;
         for (int p = 0; p < N; ++p) {
             grad_rev(p, gpx_b[p], gpy_b[p]);
             for (int k = 1; k < 5; ++k) vb[k][p] += lap_b[p] * (2.0 / 3.0);
