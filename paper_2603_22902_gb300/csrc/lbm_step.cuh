@@ -295,11 +295,21 @@ __device__ __forceinline__ void push_row_at(const KParams& P, const PopView<Pr>&
     st_pop<Pr, KIND>(P, out, s, j, (long long)y * P.nx + tx, v, 13);
 }
 
-// All nine pushes of one species, plus the outflow copies of the boundary rows.
+// All nine pushes of one species, plus the outflow copies of the boundary rows.  In a
+// tile whose cells and one-cell ring all lie inside the lattice (`interior`, the same for
+// the whole block), every population lands in the neighbour c + c_J: no wrap and no
+// boundary rule, so the general path's checks are skipped.
 template <int KIND, class Pr>
 __device__ __forceinline__ void push_species(const KParams& P, const PopView<Pr>& out, int s, int x, int y,
-                                             const typename Pr::R (&q)[9])
+                                             bool interior, const typename Pr::R (&q)[9])
 {
+    if (interior) {
+        const long long c = (long long)y * P.nx + x;
+        st_pop<Pr, KIND>(P, out, s, 0, c, q[0], 10);
+#pragma unroll
+        for (int j = 1; j < 9; ++j) st_pop<Pr, KIND>(P, out, s, j, c + (cy(j) * P.nx + cx(j)), q[j], 10);
+        return;
+    }
     push<0, KIND, Pr>(P, out, s, x, y, q[0]);
     push<1, KIND, Pr>(P, out, s, x, y, q[1]);
     push<2, KIND, Pr>(P, out, s, x, y, q[2]);
@@ -611,6 +621,8 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         return;
     }
     const PopView<Pr> pout = pop_view<Pr>(P, pout_base);
+    // the tile and its one-cell ring inside the lattice: pushes need no boundary rule
+    const bool interior = x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1;
 
     // ---- stage F: flow collision -------------------------------------------
     {
@@ -637,7 +649,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         R q[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) q[i] = rfma(wgt_r<R>(i), X[i], om1 * f[i]);
-        push_species<KIND_F, Pr>(P, pout, 0, x, y, q);
+        push_species<KIND_F, Pr>(P, pout, 0, x, y, interior, q);
     }
 
     // ---- stage F: phase-field collisions -------------------------------------
@@ -663,7 +675,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
             q[7] = rfma(wgt_r<R>(7), b0 - (bxv + byv), og1 * gq[7]);
             q[6] = rfma(wgt_r<R>(6), b0 + (byv - bxv), og1 * gq[6]);
             q[8] = rfma(wgt_r<R>(8), b0 - (byv - bxv), og1 * gq[8]);
-            push_species<KIND_G, Pr>(P, pout, 1 + pp, x, y, q);
+            push_species<KIND_G, Pr>(P, pout, 1 + pp, x, y, interior, q);
             LBM_ST(P, aout, aux_phiux(pp) * S + c, P.aux_elems, 30, (TA)(phi[pp] * ux));
             LBM_ST(P, aout, aux_phiuy(N, pp) * S + c, P.aux_elems, 31, (TA)(phi[pp] * uy));
         }
@@ -695,7 +707,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         q[8] = rfma(wgt_r<R>(8), (bd - cxy) - (cyv - cxv), oh1 * h[8]);
         // outflow rows are copied inside push_species; Dirichlet rows get their
         // incoming populations from the ghost rule below
-        push_species<KIND_H, Pr>(P, pout, N + 1, x, y, q);
+        push_species<KIND_H, Pr>(P, pout, N + 1, x, y, interior, q);
         // Dirichlet wall: ghost behind the half-way wall with T_g = 2 T_w - T, u = 0; its
         // post-collision population is h_eq(ghost) + (1 - 1/tau_h)(h_j - h_eq_j) for the
         // three directions j that enter the boundary row (one code path for both walls:
