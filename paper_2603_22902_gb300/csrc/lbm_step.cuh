@@ -457,36 +457,41 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     }
     __syncthreads();
     // ---- ghosts beyond walls / outflows ------------------------------------
-    for (int k = tid; k < W * H; k += NT) {
-        const int lx = k % W, ly = k / W;
-        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        const bool xo = !xper && (gx < 0 || gx >= nx);
-        const bool yo = !yper && (gy < 0 || gy >= ny);
-        if (!xo && !yo) continue;
-        const int sx = xo ? min(max(gx, 0), nx - 1) - x0 + 1 : lx;
-        const int sy = yo ? min(max(gy, 0), ny - 1) - y0 + 1 : ly;
-        const int wx = xo ? (gx < 0 ? 0 : 1) : -1;
-        const int wy = yo ? (gy < 0 ? 2 : 3) : -1;
-        R ph[N];
-#pragma unroll
-        for (int p = 0; p < N; ++p) ph[p] = s_phi[p][sy][sx];
-#pragma unroll
-        for (int p = 0; p < N; ++p) {
-            R corr = R(0);
-#pragma unroll
-            for (int q = 0; q < N; ++q) {
-                if (q == p) continue;
-                R cw = R(0);
-                if (wx >= 0) cw += C.wet[wx][p][q];
-                if (wy >= 0) cw += C.wet[wy][p][q];
-                corr = rfma(cw * ph[p], ph[q], corr);
+    // (none when the ring lies inside the lattice along every non-periodic axis: then
+    // the pass and its barrier are skipped by the whole block)
+    const bool ghosts = (!xper && (x0 < 1 || x0 + TX > nx - 1)) || (!yper && (y0 < 1 || y0 + TY > ny - 1));
+    if (ghosts) {
+        for (int k = tid; k < W * H; k += NT) {
+            const int lx = k % W, ly = k / W;
+            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+            const bool xo = !xper && (gx < 0 || gx >= nx);
+            const bool yo = !yper && (gy < 0 || gy >= ny);
+            if (!xo && !yo) continue;
+            const int sx = xo ? min(max(gx, 0), nx - 1) - x0 + 1 : lx;
+            const int sy = yo ? min(max(gy, 0), ny - 1) - y0 + 1 : ly;
+            const int wx = xo ? (gx < 0 ? 0 : 1) : -1;
+            const int wy = yo ? (gy < 0 ? 2 : 3) : -1;
+            R ph[N];
+    #pragma unroll
+            for (int p = 0; p < N; ++p) ph[p] = s_phi[p][sy][sx];
+    #pragma unroll
+            for (int p = 0; p < N; ++p) {
+                R corr = R(0);
+    #pragma unroll
+                for (int q = 0; q < N; ++q) {
+                    if (q == p) continue;
+                    R cw = R(0);
+                    if (wx >= 0) cw += C.wet[wx][p][q];
+                    if (wy >= 0) cw += C.wet[wy][p][q];
+                    corr = rfma(cw * ph[p], ph[q], corr);
+                }
+                s_phi[p][ly][lx] = ph[p] + corr;
             }
-            s_phi[p][ly][lx] = ph[p] + corr;
+            s_rho[ly][lx] = s_rho[sy][sx];
+            s_psi[ly][lx] = s_psi[sy][sx];
         }
-        s_rho[ly][lx] = s_rho[sy][sx];
-        s_psi[ly][lx] = s_psi[sy][sx];
+        __syncthreads();
     }
-    __syncthreads();
     if (!owned) return;
 
     const int lx = tx + 1, ly = ty + 1;
