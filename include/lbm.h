@@ -178,14 +178,6 @@ int lbm_debug_bounds(lbm_handle* h, long long* out3);
  * shape must be one of the compiled variants (LBM_EINVAL otherwise). */
 int lbm_set_tile(lbm_handle* h, int bx, int by);
 
-/* Staged loads of the 16-bit storage policies (LBM_FP16S, LBM_BF16S): with enable != 0
- * (the default) and nx a multiple of 8, each block of the step first copies its tile's
- * rows of every plane to shared memory and reads the step's data from there; with 0 it
- * reads every value from global memory.  The results are the same; it is a performance
- * switch (a tuning and testing knob, no counterpart in the paper).  Other policies ignore
- * it.  Returns LBM_EINVAL only for a NULL handle. */
-int lbm_set_staging(lbm_handle* h, int enable);
-
 /* Diagnostics sums without any allocation, for callers that cannot allocate device
  * memory when they need them: code that is recording a CUDA graph, a host that owns all
  * device memory through its own arena, a timed loop that forbids allocation latency.

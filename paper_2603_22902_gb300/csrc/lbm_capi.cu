@@ -190,7 +190,6 @@ int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_t
     P.f = round_coef(P.d);
     P.x = split_coef(P.d);
     P.dbg = nullptr;
-    P.stage = 1;
     dispatch(N, h->precision, [&](auto n, auto pr) {
         using Pr = decltype(pr);
         h->pop_bytes = (size_t)pop_set_bytes<Pr>(decltype(n)::value, P.S);
@@ -245,13 +244,6 @@ int lbm_set_tile(lbm_handle* h, int bx, int by)
         }
     }
     return fail(h, LBM_EINVAL, "tile shape not compiled (32x8, 32x4, 64x4, 16x16)");
-}
-
-int lbm_set_staging(lbm_handle* h, int enable)
-{
-    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
-    h->P.stage = enable != 0;
-    return LBM_OK;
 }
 
 int lbm_set_fields(lbm_handle* h, const double* phi, const double* T, const double* ux, const double* uy, int where)

@@ -64,7 +64,6 @@ struct KParams {
     long long rest_elems, move_elems; // elements of the rest / moving block of one population set
     long long aux_elems;          // elements of one lagged set
     unsigned long long* dbg;      // LBM_CHECK_BOUNDS builds: {violations, first site, first index}
-    int stage;                    // STAGE policies: staged loads allowed (lbm_set_staging)
 };
 
 template <class R>

@@ -18,17 +18,6 @@ static cudaError_t launch_fused_t(const KParams& P, const void* pin, void* pout,
 {
     using TA = typename Pr::TA;
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-    if constexpr (Pr::STAGE && COLLIDE) {
-        // staged copy: every 16-byte chunk of a row window must lie in one lattice row
-        if (P.stage && P.nx % 8 == 0) {
-            constexpr int bytes = StageLayout<N, TX, TY, Pr>::BYTES;
-            auto kern = fused_step_kernel<N, TX, TY, COLLIDE, Pr, true>;
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            if (e != cudaSuccess) return e;
-            kern<<<grid, TX * TY, bytes, st>>>(P, pin, pout, (const TA*)ain, (TA*)aout, ex);
-            return cudaGetLastError();
-        }
-    }
     fused_step_kernel<N, TX, TY, COLLIDE, Pr><<<grid, TX * TY, 0, st>>>(P, pin, pout, (const TA*)ain, (TA*)aout, ex);
     return cudaGetLastError();
 }

@@ -28,11 +28,6 @@
 // 1e-3 for 16-bit storage, whose rounding noise in phi is ~1e-4 (the normal is then zero
 // only in far tails, where 4 phi_p phi_q / eps < 1e-3 as well).
 //
-// STAGE: on lattices with nx a multiple of 8, the step first copies each tile's rows of
-// every plane into shared memory with 16-byte asynchronous copies and reads everything
-// from there: one round trip to memory per block instead of three (own cells, ring
-// cells, flow populations), at ~48 KB of shared memory per block (16-bit storage).
-//
 // COMPACT: compile the step for a small code footprint rather than for the most
 // instruction-level parallelism (the phase-field collision loop is not unrolled).  The
 // double-word policy needs it: its arithmetic is ~10 instructions per operation, and
@@ -59,7 +54,6 @@ struct PrecFP64 {
     static constexpr int OCC_THREADS = 512;
     static constexpr bool COH = false;
     static constexpr bool COMPACT = false;
-    static constexpr bool STAGE = false;
 };
 struct PrecFP32 {
     using R = float;
@@ -72,7 +66,6 @@ struct PrecFP32 {
     static constexpr int OCC_THREADS = 1024;
     static constexpr bool COH = false;
     static constexpr bool COMPACT = false;
-    static constexpr bool STAGE = false;
 };
 struct PrecFP16S {
     using R = float;
@@ -85,7 +78,6 @@ struct PrecFP16S {
     static constexpr int OCC_THREADS = 1024;
     static constexpr bool COH = false;
     static constexpr bool COMPACT = false;
-    static constexpr bool STAGE = true;
 };
 struct PrecBF16S {
     using R = float;
@@ -98,7 +90,6 @@ struct PrecBF16S {
     static constexpr int OCC_THREADS = 1024;
     static constexpr bool COH = false;
     static constexpr bool COMPACT = false;
-    static constexpr bool STAGE = true;
 };
 
 // FP64-class accuracy on the FP32 pipes: every population, lagged value and
@@ -116,7 +107,6 @@ struct PrecDF64 {
     static constexpr int OCC_THREADS = 768;
     static constexpr bool COH = false;
     static constexpr bool COMPACT = true;
-    static constexpr bool STAGE = false;
 };
 
 // The same policy for a launch that runs several steps (its loads must see what

@@ -57,11 +57,13 @@ __device__ __forceinline__ PopView<Pr> pop_view(const KParams& P, const void* ba
     return PopView<Pr>{(typename Pr::TR*)b, (typename Pr::TM*)(b + P.rest_elems * (long long)sizeof(typename Pr::TR))};
 }
 
-// Stored moving population (direction i != 0) of a species of kind KIND, as R.
+// Load population i of species s at cell c (dequantised to R).
 template <class Pr, int KIND>
-__device__ __forceinline__ typename Pr::R dequant(const KParams& P, typename Pr::TM q, int i)
+__device__ __forceinline__ typename Pr::R ld_pop(const KParams& P, const PopView<Pr>& v, int s, int i, long long c, int site)
 {
     using R = typename Pr::R;
+    if (i == 0) return (R)LBM_LDX(Pr::COH, P, v.rest, (long long)s * P.S + c, P.rest_elems, site);
+    const auto q = LBM_LDX(Pr::COH, P, v.move, (long long)(s * 8 + i - 1) * P.S + c, P.move_elems, site);
     if constexpr (!Pr::QUANT) {
         return (R)q;
     } else {
@@ -71,15 +73,6 @@ __device__ __forceinline__ typename Pr::R dequant(const KParams& P, typename Pr:
         if (KIND == KIND_G) return qf * w;
         return qf * (w * P.f.E_ref);
     }
-}
-
-// Load population i of species s at cell c (dequantised to R).
-template <class Pr, int KIND>
-__device__ __forceinline__ typename Pr::R ld_pop(const KParams& P, const PopView<Pr>& v, int s, int i, long long c, int site)
-{
-    using R = typename Pr::R;
-    if (i == 0) return (R)LBM_LDX(Pr::COH, P, v.rest, (long long)s * P.S + c, P.rest_elems, site);
-    return dequant<Pr, KIND>(P, LBM_LDX(Pr::COH, P, v.move, (long long)(s * 8 + i - 1) * P.S + c, P.move_elems, site), i);
 }
 
 // The same load for a second read of a population in one step: through the cached
@@ -97,7 +90,16 @@ __device__ __forceinline__ typename Pr::R ld_pop_late(const KParams& P, const Po
     (void)site;
 #endif
     if (i == 0) return (R)lbm_ld_l1<Pr::COH>(v.rest + idx);
-    return dequant<Pr, KIND>(P, lbm_ld_l1<Pr::COH>(v.move + idx), i);
+    const auto q = lbm_ld_l1<Pr::COH>(v.move + idx);
+    if constexpr (!Pr::QUANT) {
+        return (R)q;
+    } else {
+        const float w = (float)wgt(i);
+        const float qf = to_f(q);
+        if (KIND == KIND_F) return qf * (w * F_SCALE);
+        if (KIND == KIND_G) return qf * w;
+        return qf * (w * P.f.E_ref);
+    }
 }
 
 // Store population i of species s at cell c (quantised from R).
@@ -202,167 +204,32 @@ __device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>
     psi = fs * mix_sum<N, R>(phi, C.drho);
 }
 
-// Where a cell's populations and lagged values come from: the lattice planes in global
-// memory (GlobalCell), or the block's staged copy of its tile rows in shared memory
-// (StagedCell, see stage_tile).  Both give the same values.
-template <class Pr>
-struct GlobalCell {
-    const KParams& P;
-    const PopView<Pr>& pin;
-    const typename Pr::TA* __restrict__ ain;
-    long long c;
-    template <int KIND>
-    __device__ __forceinline__ typename Pr::R pop(int s, int i, int site) const
-    {
-        return ld_pop<Pr, KIND>(P, pin, s, i, c, site);
-    }
-    // a second read of a population in the same step (see ld_pop_late)
-    template <int KIND>
-    __device__ __forceinline__ typename Pr::R pop_late(int s, int i, int site) const
-    {
-        return ld_pop_late<Pr, KIND>(P, pin, s, i, c, site);
-    }
-    __device__ __forceinline__ typename Pr::R aux(int a, int site) const
-    {
-        return (typename Pr::R)LBM_LDX(Pr::COH, P, ain, a * P.S + c, P.aux_elems, site);
-    }
-};
-
-// Shared-memory copy of one tile's data (policies with STAGE, lattices with nx a multiple
-// of 8): for every plane of the population set and of the lagged set, the rows y0 - 1 ..
-// y0 + TY of a window that starts 16 bytes left of the tile and ends 16 bytes right of
-// it (8 cells of a 16-bit plane, 4 of a 32-bit one).  The window is copied in 16-byte
-// chunks with cp.async; with nx a multiple of 8 every chunk lies inside one row of the
-// lattice, starts on a 16-byte boundary, and wraps as a whole on a periodic axis.
-template <int N, int TX, int TY, class Pr>
-struct StageLayout {
-    using TR = typename Pr::TR;
-    using TM = typename Pr::TM;
-    using TA = typename Pr::TA;
-    static constexpr int H = TY + 2;
-    static constexpr int PM = 16 / (int)sizeof(TM), PR = 16 / (int)sizeof(TR), PA = 16 / (int)sizeof(TA);
-    static constexpr int WM = TX + 2 * PM, WR = TX + 2 * PR, WA = TX + 2 * PA;   // window widths (elements)
-    static constexpr int MOVE_BYTES = 8 * (N + 2) * H * WM * (int)sizeof(TM);
-    static constexpr int REST_BYTES = (N + 2) * H * WR * (int)sizeof(TR);
-    static constexpr int AUX_BYTES = naux_planes(N) * H * WA * (int)sizeof(TA);
-    static constexpr int BYTES = MOVE_BYTES + REST_BYTES + AUX_BYTES;
-    static_assert(TX % 8 == 0, "tile columns start on 16-byte boundaries of a 16-bit plane");
-    static_assert(MOVE_BYTES % 16 == 0 && REST_BYTES % 16 == 0, "16-byte aligned regions");
-};
-
-// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned).
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-}
-
-// Copy the tile's windows of every plane into stg (all threads of the block; ends with a
-// block barrier).  Rows beyond a non-periodic side are not copied: those positions are
-// ghosts, never read from stg.
-template <int N, int TX, int TY, class Pr>
-__device__ __forceinline__ void stage_tile(const KParams& P, const PopView<Pr>& pin,
-                                           const typename Pr::TA* __restrict__ ain, int x0, int y0,
-                                           unsigned char* stg)
-{
-    using L = StageLayout<N, TX, TY, Pr>;
-    constexpr int CM = L::WM * (int)sizeof(typename L::TM) / 16;   // chunks per row
-    constexpr int CR = L::WR * (int)sizeof(typename L::TR) / 16;
-    constexpr int CA = L::WA * (int)sizeof(typename L::TA) / 16;
-    constexpr int JM = 8 * (N + 2) * L::H * CM, JR = (N + 2) * L::H * CR, JA = naux_planes(N) * L::H * CA;
-    const int nx = P.nx, ny = P.ny;
-    const bool xper = P.bc[0] == PERIODIC, yper = P.bc[2] == PERIODIC;
-    for (int j = threadIdx.x; j < JM + JR + JA; j += blockDim.x) {
-        int k, ch, esz, pad, width;
-        const char* g;
-        char* d;
-        if (j < JM) {
-            k = j / CM; ch = j % CM;
-            esz = (int)sizeof(typename L::TM); pad = L::PM; width = L::WM;
-            g = reinterpret_cast<const char*>(pin.move); d = reinterpret_cast<char*>(stg);
-        } else if (j < JM + JR) {
-            k = (j - JM) / CR; ch = (j - JM) % CR;
-            esz = (int)sizeof(typename L::TR); pad = L::PR; width = L::WR;
-            g = reinterpret_cast<const char*>(pin.rest); d = reinterpret_cast<char*>(stg + L::MOVE_BYTES);
-        } else {
-            k = (j - JM - JR) / CA; ch = (j - JM - JR) % CA;
-            esz = (int)sizeof(typename L::TA); pad = L::PA; width = L::WA;
-            g = reinterpret_cast<const char*>(ain); d = reinterpret_cast<char*>(stg + L::MOVE_BYTES + L::REST_BYTES);
-        }
-        const int plane = k / L::H, r = k % L::H;
-        int gy = y0 - 1 + r;
-        if (gy < 0 || gy >= ny) {
-            if (!yper) continue;
-            gy = wrap_index(gy, ny);
-        }
-        int gx = x0 - pad + ch * (16 / esz);
-        if (gx < 0 || gx >= nx) {
-            if (!xper) continue;
-            gx = wrap_index(gx, nx);
-        }
-        cp_async16(d + (long long)k * width * esz + ch * 16, g + ((long long)plane * P.S + (long long)gy * nx + gx) * esz);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-}
-
-// A cell of the tile-with-ring (position lx, ly) read from the staged copy.
-template <int N, int TX, int TY, class Pr>
-struct StagedCell {
-    const KParams& P;
-    const unsigned char* stg;
-    int lx, ly;
-    using L = StageLayout<N, TX, TY, Pr>;
-    template <int KIND>
-    __device__ __forceinline__ typename Pr::R pop(int s, int i, int) const
-    {
-        if (i == 0) {
-            const auto* r = reinterpret_cast<const typename L::TR*>(stg + L::MOVE_BYTES);
-            return (typename Pr::R)r[(s * L::H + ly) * L::WR + lx - 1 + L::PR];
-        }
-        const auto* m = reinterpret_cast<const typename L::TM*>(stg);
-        return dequant<Pr, KIND>(P, m[((s * 8 + i - 1) * L::H + ly) * L::WM + lx - 1 + L::PM], i);
-    }
-    template <int KIND>
-    __device__ __forceinline__ typename Pr::R pop_late(int s, int i, int site) const
-    {
-        return pop<KIND>(s, i, site);
-    }
-    __device__ __forceinline__ typename Pr::R aux(int a, int) const
-    {
-        const auto* x = reinterpret_cast<const typename L::TA*>(stg + L::MOVE_BYTES + L::REST_BYTES);
-        return (typename Pr::R)x[(a * L::H + ly) * L::WA + lx - 1 + L::PA];
-    }
-};
-
 // Stage A + B of one cell of the tile or its ring: phi_p, rho H, f_l, T, rho and psi.
 // f_l is the FP64 map's (map_cell), the rest of eq. 2 runs in R.  T is needed only for the tile's own
 // cells, but almost every warp holds both kinds, so it is computed for all (a branch on
 // the kind would run both versions of the map).
-template <int N, class Pr, class Src>
-__device__ __forceinline__ void cell_moments(const KParams& P, const Src& src, typename Pr::R (&phi)[N],
-                                             typename Pr::R& rhoH, typename Pr::R& fl, typename Pr::R& T,
-                                             typename Pr::R& rho, typename Pr::R& psi)
+template <int N, class Pr>
+__device__ __forceinline__ void cell_moments(const KParams& P, const PopView<Pr>& pin,
+                                             const typename Pr::TA* __restrict__ ain, long long c,
+                                             typename Pr::R (&phi)[N], typename Pr::R& rhoH, typename Pr::R& fl,
+                                             typename Pr::R& T, typename Pr::R& rho, typename Pr::R& psi)
 {
     using R = typename Pr::R;
     using K = exact_t<R>;
-    const R mdm = src.aux(aux_mdot(), 1);
-    const R Qm = src.aux(aux_Q(), 2);
+    const long long S = P.S;
+    const R mdm = (R)LBM_LDX(Pr::COH, P, ain, aux_mdot() * S + c, P.aux_elems, 1);
+    const R Qm = (R)LBM_LDX(Pr::COH, P, ain, aux_Q() * S + c, P.aux_elems, 2);
     const R iden = R(1) / (R(1) - K(0.5) * mdm);
 #pragma unroll
     for (int p = 0; p < N; ++p) {
         R s = R(0);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s += src.template pop<KIND_G>(1 + p, i, 3);
+        for (int i = 0; i < 9; ++i) s += ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 3);
         phi[p] = s * iden;
     }
     R sh = R(0);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) sh += src.template pop<KIND_H>(N + 1, i, 4);
+    for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 4);
     rhoH = rfma(K(0.5), Qm, sh);
     map_cell<N, Pr, true>(P, phi, rhoH, fl, T);
     const Coef<R>& C = coef<R>(P);
@@ -472,25 +339,22 @@ __device__ __forceinline__ void push_species(const KParams& P, const PopView<Pr>
 #define LBM_OCC(Pr) (Pr::OCC_THREADS)
 #endif
 // Shared-memory elements of type R that step_tile needs: phi_p, rho and psi on the
-// tile and its one-cell ring, and (COMPACT and STAGE policies) rho H, f_l, T of the tile's
-// cells.
+// tile and its one-cell ring, and (COMPACT policies) rho H, f_l, T of the tile's cells.
 template <int N, int TX, int TY, class Pr>
 __host__ __device__ constexpr int tile_smem_elems()
 {
-    return (N + 2) * (TX + 2) * (TY + 2) + (Pr::COMPACT || Pr::STAGE ? 3 * TX * TY : 0);
+    return (N + 2) * (TX + 2) * (TY + 2) + (Pr::COMPACT ? 3 * TX * TY : 0);
 }
 
 // One TX x TY tile (tile column bx, row by) of one time step, run by a block of
-// TX * TY threads; smem holds tile_smem_elems<N, TX, TY, Pr>() elements of shared memory,
-// and, with STAGED, stg holds StageLayout<N, TX, TY, Pr>::BYTES bytes (16-byte aligned) for
-// the staged copy of the tile's data (then nx must be a multiple of 8).
+// TX * TY threads; smem holds tile_smem_elems<N, TX, TY, Pr>() elements of shared memory.
 // Every thread of the block must call it (it holds two block barriers); the caller
 // places a block barrier before smem is used again.
-template <int N, int TX, int TY, bool COLLIDE, class Pr, bool STAGED = false>
+template <int N, int TX, int TY, bool COLLIDE, class Pr>
 __device__ __forceinline__ void step_tile(const KParams& P, const void* __restrict__ pin_base,
                                           void* __restrict__ pout_base, const typename Pr::TA* __restrict__ ain,
                                           typename Pr::TA* __restrict__ aout, const ExportPtrs& ex, int bx, int by,
-                                          typename Pr::R* smem, unsigned char* stg = nullptr)
+                                          typename Pr::R* smem)
 {
     using R = typename Pr::R;
     using K = exact_t<R>;
@@ -532,23 +396,16 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         return !beyond;
     };
     R phi[N], rhoH, fl, T, rho, psi, mu, lam, cp, chi;
-    if constexpr (Pr::COMPACT || STAGED) {
+    if constexpr (Pr::COMPACT) {
         // ---- stages A + B: one code path for all (TX + 2)(TY + 2) positions, so that
-        // the moments are compiled once; the own cells' rho H, f_l, T go to shared memory.
-        // STAGED: the tile's data is first copied to shared memory in one pass of
-        // asynchronous copies (a single round trip to memory), and every read of the step
-        // comes from that copy.
-        if constexpr (STAGED) stage_tile<N, TX, TY, Pr>(P, pin, ain, x0, y0, stg);
-#pragma unroll(Pr::COMPACT ? 1 : 2)
+        // the moments are compiled once; the own cells' rho H, f_l, T go to shared memory
+#pragma unroll 1
         for (int k = tid; k < W * H; k += NT) {
             const int lx = k % W, ly = k / W;
             long long cell;
             if (!locate(lx, ly, cell)) continue;
             R ph[N], rH, flv, Tv, r, ps;
-            if constexpr (STAGED)
-                cell_moments<N, Pr>(P, StagedCell<N, TX, TY, Pr>{P, stg, lx, ly}, ph, rH, flv, Tv, r, ps);
-            else
-                cell_moments<N, Pr>(P, GlobalCell<Pr>{P, pin, ain, cell}, ph, rH, flv, Tv, r, ps);
+            cell_moments<N, Pr>(P, pin, ain, cell, ph, rH, flv, Tv, r, ps);
 #pragma unroll
             for (int p = 0; p < N; ++p) s_phi[p][ly][lx] = ph[p];
             s_rho[ly][lx] = r;
@@ -575,7 +432,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
             s_psi[ly][lx] = ps;
         };
         if (owned) {
-            cell_moments<N, Pr>(P, GlobalCell<Pr>{P, pin, ain, (long long)y * nx + x}, phi, rhoH, fl, T, rho, psi);
+            cell_moments<N, Pr>(P, pin, ain, (long long)y * nx + x, phi, rhoH, fl, T, rho, psi);
             const R fs = R(1) - fl;
             mu = rfma(fs, mix_sum<N, R>(phi, C.mu_s), fl * mix_sum<N, R>(phi, C.mu_l));
             lam = rfma(fs, mix_sum<N, R>(phi, C.lam_s), fl * mix_sum<N, R>(phi, C.lam_l));
@@ -639,7 +496,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
 
     const int lx = tx + 1, ly = ty + 1;
     const long long c = (long long)y * nx + x;
-    if constexpr (Pr::COMPACT || STAGED) {
+    if constexpr (Pr::COMPACT) {
         // ---- own cell: the rest of eq. 2 ---------------------------------------
 #pragma unroll
         for (int p = 0; p < N; ++p) phi[p] = s_phi[p][ly][lx];
@@ -727,14 +584,9 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     }
 
     // ---- stage E: flow macroscopics ----------------------------------------
-    // the own cell's populations and lagged values, read a second time in this step
-    const auto own = [&]() {
-        if constexpr (STAGED) return StagedCell<N, TX, TY, Pr>{P, stg, lx, ly};
-        else return GlobalCell<Pr>{P, pin, ain, c};
-    }();
     R f[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = own.template pop_late<KIND_F>(0, i, 5);
+    for (int i = 0; i < 9; ++i) f[i] = ld_pop_late<Pr, KIND_F>(P, pin, 0, i, c, 5);
     const R jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
     const R jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
     const R sum_f = ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
@@ -750,7 +602,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     const R usx = rfma(K(0.5), Fx, jx) * irho, usy = rfma(K(0.5), Fy, jy) * irho;
     const R fpx = chi * (C.us[0] - usx), fpy = chi * (C.us[1] - usy);
     const R ux = rfma(K(0.5), fpx, usx), uy = rfma(K(0.5), fpy, usy);
-    const R psim = own.aux(aux_psi(), 14);
+    const R psim = (R)LBM_LDX(Pr::COH, P, ain, aux_psi() * S + c, P.aux_elems, 14);
     const R mdot = -((psi - psim) + (ux * gsx + uy * gsy)) * irho;
     const R Ssrc = rfma(rho, mdot, ux * grx + uy * gry);
     const R Lxx = rfma(K(2) * ux, Fx, Ssrc * R(1.0 / 3.0));
@@ -812,9 +664,9 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         for (int pp = 0; pp < N; ++pp) {
             R gq[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) gq[i] = own.template pop_late<KIND_G>(1 + pp, i, 6);
-            const R Dx = phi[pp] * ux - own.aux(aux_phiux(pp), 15);
-            const R Dy = phi[pp] * uy - own.aux(aux_phiuy(N, pp), 16);
+            for (int i = 0; i < 9; ++i) gq[i] = ld_pop_late<Pr, KIND_G>(P, pin, 1 + pp, i, c, 6);
+            const R Dx = phi[pp] * ux - (R)LBM_LDX(Pr::COH, P, ain, aux_phiux(pp) * S + c, P.aux_elems, 15);
+            const R Dy = phi[pp] * uy - (R)LBM_LDX(Pr::COH, P, ain, aux_phiuy(N, pp) * S + c, P.aux_elems, 16);
             const R b0 = og * phi[pp] + kg * phi[pp] * mdot;
             const R bxv = K(3) * og * phi[pp] * ux + kg * rfma(K(3), Dx, Rx[pp]);
             const R byv = K(3) * og * phi[pp] * uy + kg * rfma(K(3), Dy, Ry[pp]);
@@ -838,7 +690,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     {
         R h[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) h[i] = own.template pop_late<KIND_H>(N + 1, i, 7);
+        for (int i = 0; i < 9; ++i) h[i] = ld_pop_late<Pr, KIND_H>(P, pin, N + 1, i, c, 7);
         const R Z = rho * cp * T, E = C.E_ref * T;
         const R kh = rfma(K(-0.5), oh, R(1)), oh1 = R(1) - oh;
         const R Zm = Z * mdot;
@@ -890,18 +742,14 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     }
 }
 
-// Dynamic shared memory of the staged kernels (StageLayout::BYTES at launch).
-extern __shared__ __align__(16) unsigned char lbm_stage_smem[];
-
 // One launch = one time step of one lattice, one block per tile.
-template <int N, int TX, int TY, bool COLLIDE, class Pr, bool STAGED = false>
+template <int N, int TX, int TY, bool COLLIDE, class Pr>
 __global__ void __launch_bounds__(TX * TY, (LBM_OCC(Pr) + TX * TY - 1) / (TX * TY))
 fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __restrict__ pout_base,
                   const typename Pr::TA* __restrict__ ain, typename Pr::TA* __restrict__ aout, ExportPtrs ex)
 {
     __shared__ typename Pr::R smem[tile_smem_elems<N, TX, TY, Pr>()];
-    step_tile<N, TX, TY, COLLIDE, Pr, STAGED>(P, pin_base, pout_base, ain, aout, ex, blockIdx.x, blockIdx.y, smem,
-                                              STAGED ? lbm_stage_smem : nullptr);
+    step_tile<N, TX, TY, COLLIDE, Pr>(P, pin_base, pout_base, ain, aout, ex, blockIdx.x, blockIdx.y, smem);
 }
 
 }  // namespace lbm

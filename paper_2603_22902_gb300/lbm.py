@@ -108,7 +108,6 @@ def library():
             lib.lbm_get_steps.argtypes = [_VP]
             lib.lbm_get_steps.restype = ctypes.c_longlong
             lib.lbm_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
-            lib.lbm_set_staging.argtypes = [_VP, ctypes.c_int]
             lib.lbm_debug_bounds.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong)]
             lib.lbm_debug_bounds.restype = ctypes.c_int
             lib.lbm_last_error.argtypes = [_VP]
@@ -127,7 +126,7 @@ def library():
             lib.lbm_batch_last_error.restype = ctypes.c_char_p
             lib.lbm_batch_destroy.argtypes = [_VP]
             for name in ("lbm_create", "lbm_set_stream", "lbm_set_fields", "lbm_step", "lbm_get_fields",
-                         "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile", "lbm_set_staging",
+                         "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile",
                          "lbm_batch_create", "lbm_batch_set_stream", "lbm_batch_set_plan", "lbm_batch_get_plan",
                          "lbm_batch_step", "lbm_batch_sync", "lbm_batch_autotune", "lbm_adjoint_fl_loss"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -211,10 +210,6 @@ def lbm_get_steps(h) -> int:
 
 def lbm_set_tile(h, bx, by):
     return _check(library().lbm_set_tile(h, bx, by), h)
-
-
-def lbm_set_staging(h, enable):
-    return _check(library().lbm_set_staging(h, int(bool(enable))), h)
 
 
 def lbm_debug_bounds(h):
