@@ -138,3 +138,15 @@ def test_df64_interface_limits(lbm):
         lbm.Batch([s])
     assert e.value.code == lbm.LBM_EINVAL
     s.close()
+
+
+def test_df64_full_size_compound_and_impurities(lbm):
+    # the compound drop (1024^2, N = 3) and the impurity pool (512^2, N = 4, 24 disks), a
+    # few steps each, whole fields against the oracle
+    for name, case, steps in (("compound_1024", W.compound_drop(), 2),
+                              ("impurity_pool_512", W.impurity_freeze(), 3)):
+        G, d = run_df64(lbm, case, steps)
+        errs = errors(G, oracle.Oracle(case).step(steps).fields(), case)
+        print(name, steps, "steps", errs)
+        assert d["nonfinite"] == 0
+        assert within(errs), (name, errs)
