@@ -179,8 +179,9 @@ int lbm_debug_bounds(lbm_handle* h, long long* out3);
 int lbm_set_tile(lbm_handle* h, int bx, int by);
 
 /* Diagnostics sums without any allocation, for callers that cannot allocate device
- * memory when they need them: code that is recording a CUDA graph, a host that owns all
- * device memory through its own arena, a timed loop that forbids allocation latency.
+ * memory when they need them: a host that owns all device memory through its own arena
+ * or pool and forbids other allocators, a service whose device memory is fixed when it
+ * starts, a timed loop that forbids allocation latency.
  * (The paper has no counterpart: this is a service of the library.)
  * Inputs are caller-owned device fields of one lattice: phi [N][ny][nx] and the liquid
  * fraction fl [ny][nx] (as written by lbm_get_fields with LBM_DEVICE); out is a

@@ -3,10 +3,10 @@
 //
 // lbm_get_diagnostics reduces the state of a handle in two passes through a scratch
 // buffer of block partial sums that lbm_create allocates with cudaMalloc.  Some callers
-// cannot allocate at the time they need these sums: code that is recording a CUDA graph
-// (an allocation would break or be baked into the capture), a host embedding that owns
-// the device memory through its own arena and forbids other allocators, or a timed loop
-// where allocation latency is not allowed.  This entry point computes the same sums from
+// cannot allocate at the time they need these sums: a host embedding that owns the
+// device memory through its own arena or pool and forbids other allocators, a service
+// whose device memory is fixed when it starts, or a timed loop where allocation latency
+// is not allowed.  This entry point computes the same sums from
 // caller-owned device fields into a caller-owned device result, using a scratch array
 // that lives in this library's device image instead of the heap.
 #include <cuda_runtime.h>

@@ -1,6 +1,6 @@
 """lbm_field_sums_noalloc: the diagnostics sums for callers that cannot allocate device
-memory (for instance while recording a CUDA graph, or inside a host that owns all device
-memory through its own arena).  The entry point takes caller-owned device fields and a
+memory (for instance a host that owns all device memory through its own arena or pool, or
+a service whose device memory is fixed when it starts).  The entry point takes caller-owned device fields and a
 caller-owned device result and keeps its block partial sums in a fixed-size array in the
 library's device image, so it never calls an allocator.
 
