@@ -59,13 +59,14 @@ FP64_PIPE_PEAK_GINST = 152 * 2 * 2.070
 # and is bound by this issue rate rather than by any one pipe or by HBM.
 ISSUE_PEAK_GWINST = 152 * 4 * 2.070
 # Per lattice update of the fused step kernel, from one ncu capture of the kernel built
-# from the sources with digest `digest` (sessile drop 512^2, N = 2, 32 x 8 tiles):
+# from the kernel sources with digest `digest` (build.kernel_digest; sessile drop 512^2,
+# N = 2, 32 x 8 tiles):
 # FP64-pipe thread-instructions, FP64 flop (DFMA = 2, DADD / DMUL = 1), warp-instructions
 # issued, FP32 thread-instructions (FADD + FMUL + FFMA) and DRAM bytes.
 # A changed kernel has another digest, and then these counts are not reported.
 # (DRAM bytes are what ncu saw during the launch: part of the writes of a launch is
 # still in L2 when it ends and reaches DRAM during the next one.)
-_D = "18cdb20a67c78c85888fcdbaa82b3e58c0cb19527c9b165b838d04702942d206"
+_D = "ad87ef452fddf94b78bb3b732b8bae53c0d89447a4ef253d5b790d1cd6207ee3"
 NCU_COUNTS = {
     ("fp64", 2): {"digest": _D, "fp64_inst": 487.0, "fp64_flop": 660.9, "warp_inst": 102.4, "dram_bytes": 518.4},
     ("df64", 2): {"digest": _D, "fp64_inst": 58.6, "warp_inst": 185.6, "fp32_inst": 4502.1, "dram_bytes": 653.3},
@@ -84,7 +85,7 @@ def load_peaks():
 
 def kernel_digest():
     from paper_2603_22902_gb300 import build as B
-    return B._sources_digest()
+    return B.kernel_digest()
 
 
 def ncu_counts(precision, N):

@@ -40,6 +40,20 @@ def _sources_digest(extra=()) -> str:
     return h.hexdigest()
 
 
+def kernel_digest() -> str:
+    """Digest of what the device kernels are compiled from: the headers of csrc/ and the
+    kernel units lbm_kernels_*.cu (the C ABI units and include/lbm.h are host code that
+    no kernel includes), with the compiler flags.  Measured per-kernel counts are tied to
+    it."""
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith(".cuh") or (name.startswith("lbm_kernels_") and name.endswith(".cu")):
+            with open(os.path.join(CSRC, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, check_bounds: bool = False) -> str:
     """Compile (if sources changed) and return the path of liblbm_gb300.so.
 
