@@ -132,7 +132,8 @@ __device__ __forceinline__ void st_pop(const KParams& P, const PopView<Pr>& v, i
 // As and Al), the FP64 map would return f_l = 1 or 0 as well, and T is then taken from
 // the same branch formula in FP32.  Only the other cells (the mushy band, values near a
 // threshold, phase-changing material below FP32 range) run the FP64 map, so f_l is the
-// FP64 map's value in every cell.
+// FP64 map's value in every cell.  The double-word policy screens its high words the same
+// way and takes T of a decided cell in double-word arithmetic.
 template <int N, class Pr, bool WANT_T>
 __device__ __forceinline__ void map_cell(const KParams& P, const typename Pr::R (&phi)[N], typename Pr::R rhoH,
                                          typename Pr::R& fl, typename Pr::R& T)
@@ -160,6 +161,37 @@ __device__ __forceinline__ void map_cell(const KParams& P, const typename Pr::R 
         if (Lv > 0.0f && rhoH < As - tol) {
             fl = 0.0f;
             if (WANT_T) T = rhoH / rcs;
+            return;
+        }
+    } else if constexpr (std::is_same<R, df64>::value) {
+        // the same screen on the high words (within 2^-24 of the double words); T of a
+        // decided cell from the branch formula in double-word arithmetic
+        const Coef<float>& Cf = P.f;
+        float rs = 0.0f, rl = 0.0f, cs = 0.0f, cl = 0.0f, Lv = 0.0f;
+#pragma unroll
+        for (int p = 0; p < N; ++p) {
+            rs = fmaf(phi[p].hi, Cf.rho_s[p], rs);
+            rl = fmaf(phi[p].hi, Cf.rho_l[p], rl);
+            cs = fmaf(phi[p].hi, Cf.cp_s[p], cs);
+            cl = fmaf(phi[p].hi, Cf.cp_l[p], cl);
+            Lv = fmaf(phi[p].hi, Cf.rhoL[p], Lv);
+        }
+        const float rcs = rs * cs, rcl = rl * cl, h = rhoH.hi;
+        const float As = rcs * Cf.T_sol, Al = fmaf(rcl, Cf.T_liq, Lv);
+        const float tol = 1e-5f * (fabsf(As) + fabsf(rcl * Cf.T_liq) + fabsf(Lv) + fabsf(h)) + 1e-30f;
+        const Coef<df64>& C = P.x;
+        if (h > Al + tol) {
+            fl = R(1);
+            if (WANT_T) {
+                const R rcl_d = mix_sum<N, R>(phi, C.rho_l) * mix_sum<N, R>(phi, C.cp_l);
+                const R Al_d = rfma(rcl_d, C.T_liq, mix_sum<N, R>(phi, C.rhoL));
+                T = C.T_liq + (rhoH - Al_d) / rcl_d;
+            }
+            return;
+        }
+        if (Lv > 0.0f && h < As - tol) {
+            fl = R(0);
+            if (WANT_T) T = rhoH / (mix_sum<N, R>(phi, C.rho_s) * mix_sum<N, R>(phi, C.cp_s));
             return;
         }
     }
