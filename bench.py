@@ -55,21 +55,22 @@ def bytes_per_lu(N: int, precision: str = "fp64") -> int:
 # per second (x 2 flop per FMA = 1.259 TFLOP/s).
 FP64_PIPE_PEAK_GINST = 152 * 2 * 2.070
 # Instruction issue: 152 SMs x 4 schedulers x 1 warp-instruction per clock x 2.07 GHz.
-# The double-word step runs ~4700 FP32 instructions per lattice update on the FP32 pipes
+# The double-word step runs ~4400 FP32 instructions per lattice update on the FP32 pipes
 # and is bound by this issue rate rather than by any one pipe or by HBM.
 ISSUE_PEAK_GWINST = 152 * 4 * 2.070
 # Per lattice update of the fused step kernel, from one ncu capture of the kernel built
 # from the kernel sources with digest `digest` (build.kernel_digest; sessile drop 512^2,
 # N = 2, 32 x 8 tiles):
 # FP64-pipe thread-instructions, FP64 flop (DFMA = 2, DADD / DMUL = 1), warp-instructions
-# issued, FP32 thread-instructions (FADD + FMUL + FFMA) and DRAM bytes.
+# issued, FP32 thread-instructions (FADD + FADD2 + FMUL + FFMA; a packed FADD2 counts
+# once) and DRAM bytes.
 # A changed kernel has another digest, and then these counts are not reported.
 # (DRAM bytes are what ncu saw during the launch: part of the writes of a launch is
 # still in L2 when it ends and reaches DRAM during the next one.)
-_D = "ac13539b9a877589c35e9ce6c0f00ca0774380c0f59afe2f5d64298787daaf13"
+_D = "00f70de4de83587cb0eac30dfb22662dec9cfa0d1ec3708e1645489214a053d3"
 NCU_COUNTS = {
-    ("fp64", 2): {"digest": _D, "fp64_inst": 487.0, "fp64_flop": 660.9, "warp_inst": 102.4, "dram_bytes": 520.0},
-    ("df64", 2): {"digest": _D, "fp64_inst": 0.08, "warp_inst": 185.2, "fp32_inst": 4723.1, "dram_bytes": 636.4},
+    ("fp64", 2): {"digest": _D, "fp64_inst": 487.0, "fp64_flop": 660.9, "warp_inst": 102.4, "dram_bytes": 518.7},
+    ("df64", 2): {"digest": _D, "fp64_inst": 0.08, "warp_inst": 176.0, "fp32_inst": 4406.3, "dram_bytes": 645.9},
     ("fp16s", 2): {"digest": _D, "fp64_inst": 0.06, "fp64_flop": 0.02, "warp_inst": 50.8, "dram_bytes": 108.4},
 }
 
