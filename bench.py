@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -110,10 +111,12 @@ def make_case(name):
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, directory=None):
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to `directory` (--clocks-dir) when given, else to a temporary
+        # directory; the JSON line carries their summary either way
+        self.path = os.path.join(directory or tempfile.gettempdir(), f"clocks_rank{index}.csv")
 
     def start(self):
         try:
@@ -250,7 +253,7 @@ def run_gpu(args):
     barrier(world)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_dir)
     clocks.start()
     torch.cuda.synchronize()
     barrier(world)
@@ -338,7 +341,7 @@ def run_gpu(args):
             "clocks": clk, "wall_s_timed_loop": round(t_wall, 4),
         }
         if rp is not None:
-            # "reduced_precision": FP16 storage (the benchmark spec's reduced-precision form);
+            # "reduced_precision": FP16 storage (the reduced-precision form of the step);
             # "double_word": FP64-class accuracy on the FP32 pipes (parity-tested to 1e-10)
             if "fp16s" in rp:
                 line["reduced_precision"] = rp.pop("fp16s")
@@ -444,7 +447,7 @@ def run_batch(args):
     barrier(world)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(calls)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(calls)]
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_dir)
     clocks.start()
     torch.cuda.synchronize()
     barrier(world)
@@ -529,6 +532,7 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=None, help="directory for the raw nvidia-smi clock samples")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
