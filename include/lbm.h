@@ -59,7 +59,8 @@ extern "C" {
 #define LBM_FP16S 2 /* FP16 storage of shifted populations, FP32 arithmetic */
 #define LBM_BF16S 3 /* BF16 storage of shifted populations, FP32 arithmetic */
 #define LBM_DF64 4  /* double-word (FP32 pair, ~48-bit) storage and arithmetic on the FP32
-                       pipes, the enthalpy map in FP64; 32x8 tiles only, no batch form */
+                       pipes, the enthalpy map in FP64 where it decides f_l; held to the
+                       FP64 parity bar; 32x8 tiles only, no batch form */
 
 #define LBM_HOST 0
 #define LBM_DEVICE 1
@@ -174,8 +175,10 @@ long long lbm_get_steps(const lbm_handle* h);
  * Synchronises the handle's stream.  Returns LBM_EINVAL in normal builds. */
 int lbm_debug_bounds(lbm_handle* h, long long* out3);
 
-/* Tile shape (bx, by) of the fused step kernel; 0, 0 restores the default.  The
- * shape must be one of the compiled variants (LBM_EINVAL otherwise). */
+/* Tile shape (bx, by) of the fused step kernel; 0, 0 restores the default (32x8).  The
+ * shape must be one of the compiled variants, 32x8, 32x4, 64x4 or 16x16, and 32x8 for
+ * an LBM_DF64 handle (LBM_EINVAL otherwise).  Results of different shapes agree to
+ * rounding, not bit for bit (each shape is compiled on its own). */
 int lbm_set_tile(lbm_handle* h, int bx, int by);
 
 /* Diagnostics sums without any allocation, for callers that cannot allocate device
