@@ -43,13 +43,18 @@ def _sources_digest(extra=()) -> str:
 def kernel_digest() -> str:
     """Digest of what the device kernels are compiled from: the headers of csrc/ and the
     kernel units lbm_kernels_*.cu (the C ABI units and include/lbm.h are host code that
-    no kernel includes), with the compiler flags.  Measured per-kernel counts are tied to
-    it."""
+    no kernel includes), with comments removed, and the compiler flags.  Measured
+    per-kernel counts are tied to it."""
+    import re
     h = hashlib.sha256()
     for name in sorted(os.listdir(CSRC)):
         if name.endswith(".cuh") or (name.startswith("lbm_kernels_") and name.endswith(".cu")):
-            with open(os.path.join(CSRC, name), "rb") as fh:
-                h.update(name.encode() + fh.read())
+            with open(os.path.join(CSRC, name)) as fh:
+                text = fh.read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", "", text)
+            text = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+            h.update(name.encode() + text.encode())
     h.update(" ".join(ARCH + FLAGS).encode())
     return h.hexdigest()
 

@@ -8,19 +8,24 @@
 // set B (ping-pong), so it is race-free across blocks.
 //
 // Per block (a TX x TY tile, one thread per cell):
-//   1. each thread loads its cell's populations into registers and evaluates the
-//      moments (phi_p = sum g / (1 - mdot'/2), rho H = sum h + Q'/2), the mixture
-//      rule (eq. 2) and the enthalpy map (eq. H, always FP64);
-//   2. the 1-cell halo ring recomputes phi_p, rho, psi of the neighbour cells from
-//      their own populations (no second kernel, no extra HBM field), and ghost
-//      values beyond walls/outflows are filled (zero gradient; wetting for phi_p);
+//   1. the moments of every cell of the tile and of its 1-cell ring (phi_p = sum g /
+//      (1 - mdot'/2), rho H = sum h + Q'/2), the mixture rule (eq. 2) and the enthalpy
+//      map (eq. H): the ring cells recompute phi_p, rho, psi from their own populations
+//      (no second kernel, no extra HBM field).  FP64 / FP32 / 16-bit policies evaluate the
+//      own cell in registers and share the ring out; the compact (double-word) policy runs
+//      one loop over all positions so that this code exists once.  f_l is always the FP64
+//      map's; the FP32-arithmetic and double-word policies screen eq. H in FP32 first and
+//      run the FP64 map only where the screen cannot decide f_l (map_cell);
+//   2. ghost values beyond walls/outflows are filled (zero gradient; wetting for phi_p),
+//      skipped by tiles that have none;
 //   3. the isotropic 9-point gradients / Laplacians of phi_p, rho, psi come from
 //      shared memory; then the pairwise normals n_pq, R_p, mu_p, F_s (Section 2),
 //      u*, the penalty force, u, mdot, S, Lambda, p (Section 3), and the three BGK
 //      collisions with their source terms;
 //   4. post-collision populations are pushed to the neighbours' slots of set B with
 //      the boundary rules (bounce-back, outflow copy, non-equilibrium extrapolation
-//      of the Dirichlet temperature), and the lagged planes are written.
+//      of the Dirichlet temperature; tiles whose ring lies inside the lattice skip the
+//      checks), and the lagged planes are written.
 // No address outside the planes is ever formed, not even for a value that is then
 // not used: the compiler may issue loads ahead of the branch that guards them.
 #pragma once
