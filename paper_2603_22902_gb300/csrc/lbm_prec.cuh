@@ -15,7 +15,9 @@
 //                                         density ratio of 100 turned into 1 % of rho and of T)
 //   h_i  -> h_i / (w_i rho_ref c_p,ref)  (= T + O(u) away from walls)
 // Lagged planes are stored as TA.  Arithmetic of the collision runs in R; the
-// enthalpy -> (f_l, T) map always runs in FP64.
+// liquid fraction always comes from the FP64 enthalpy map (eq. H); policies that compute
+// in FP32 or double words screen the cell first and run the FP64 map only where the
+// screen cannot decide f_l (map_cell in lbm_step.cuh).
 //
 // NGUARD: the pairwise normal n_pq = grad phi_pq / |grad phi_pq| is set to zero where
 // |grad phi_pq| is below NGUARD times its own scale (phi_q |grad phi_p| + phi_p |grad phi_q|),
@@ -94,7 +96,8 @@ struct PrecBF16S {
 
 // FP64-class accuracy on the FP32 pipes: every population, lagged value and
 // coefficient is a double word (lbm_df64.cuh), 8 bytes like FP64, and the collision
-// arithmetic runs in double-word arithmetic; the eq. H map stays in FP64.  The guard of
+// arithmetic runs in double-word arithmetic; f_l comes from the FP64 eq. H map where
+// the screen cannot decide it, T of a decided cell from double words.  The guard of
 // the pairwise normal is the oracle's.
 struct PrecDF64 {
     using R = df64;
