@@ -259,9 +259,11 @@ int lbm_adjoint_fl_loss(lbm_handle* h, const double* phi0, const double* T0, con
  * - The batch does not own the handles. They must outlive it. */
 typedef struct lbm_batch lbm_batch;
 
-#define LBM_BATCH_PERSISTENT 0 /* one cooperative launch per tile-shape group and call,
-                                  replayed as a CUDA graph; grid barrier between steps */
+#define LBM_BATCH_PERSISTENT 0 /* one cooperative launch per tile-shape group and call;
+                                  grid barrier between steps */
 #define LBM_BATCH_PER_STEP 1   /* one launch per tile-shape group and step */
+/* Either form: the launches of a call are captured into a CUDA graph the first time a
+ * call of that length runs, and the graph is replayed by later calls of that length. */
 
 /* Size classes of a case, by cells nx * ny: <= 128^2, <= 256^2, <= 384^2, larger. */
 #define LBM_BATCH_CLASSES 4
@@ -270,7 +272,7 @@ typedef struct {
     int mode;                          /* LBM_BATCH_PERSISTENT or LBM_BATCH_PER_STEP */
     int blocks_per_sm;                 /* persistent grid: resident blocks per SM, 0 = all that fit */
     int tile[LBM_BATCH_CLASSES][2];    /* tile (bx, by) per size class: 32x8, 64x4 or 16x16 */
-    int graph;                         /* out: 1 when the persistent launches replay a CUDA graph */
+    int graph;                         /* out: 1 when the calls replay a CUDA graph */
 } lbm_batch_plan;
 
 /* Build a batch over ncases handles, owned by the caller.

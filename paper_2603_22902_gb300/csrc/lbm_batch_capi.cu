@@ -1,6 +1,6 @@
 // lbm_batch_capi.cu -- batches of independent cases (the lbm_batch_* calls of
 // include/lbm.h): work-list tables, ping-pong bookkeeping of the member handles,
-// graph capture of the persistent launches, and the plan autotuner.
+// graph capture of the launches of a call (either form), and the plan autotuner.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -63,10 +63,12 @@ struct lbm_batch {
     unsigned char* d_parity = nullptr;     // [NKIND]
     unsigned int* d_bar = nullptr;         // [NKIND][2]
     int* d_status = nullptr;
-    // graph of the persistent launches of one call length
+    // graph of the launches of one call length, for the mode it was captured in
     cudaGraphExec_t exec = nullptr;
     long graph_steps = -1;
-    bool graph_ok = true;
+    int graph_mode = -1;
+    bool graph_ok = true;          // persistent form (a cooperative launch may refuse capture)
+    bool graph_ok_step = true;     // per-step form
     cudaStream_t stream = nullptr, capture = nullptr;
     std::string err;
 };
@@ -95,6 +97,7 @@ static void drop_graph(lbm_batch* b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
     b->graph_steps = -1;
+    b->graph_mode = -1;
 }
 
 static void free_tables(lbm_batch* b)
@@ -227,15 +230,49 @@ static int enqueue_persistent(lbm_batch* b, int nsteps, cudaStream_t st)
     return LBM_OK;
 }
 
-static int run_persistent(lbm_batch* b, int nsteps)
+// Flip every group's parity byte on the device (the per-step form after an odd number of
+// steps), so that a captured call replays correctly whatever the parity it starts from.
+__global__ void flip_parity_kernel(unsigned char* parity, int n)
 {
-    if (b->graph_ok && (b->exec == nullptr || b->graph_steps != nsteps)) {
+    if (threadIdx.x < n) parity[threadIdx.x] ^= 1;
+}
+
+// The per-step launches of one call: one launch per group and step.
+static int enqueue_per_step(lbm_batch* b, int nsteps, cudaStream_t st)
+{
+    for (int s = 0; s < nsteps; ++s)
+        for (int g = 0; g < NKIND; ++g) {
+            if (b->group_tiles[g] == 0) continue;
+            const BatchTable T = group_table(b, g);
+            const int kind = KIND_TILE[g];
+            cudaError_t e = dispatch(b->N, b->precision, [&](auto n, auto pr) {
+                return launch_batch_step<decltype(n)::value, decltype(pr)>(T, kind, s, st);
+            });
+            if (e != cudaSuccess) return bcuda(b, e, "batch step launch");
+        }
+    if (nsteps & 1) {
+        flip_parity_kernel<<<1, 32, 0, st>>>(b->d_parity, NKIND);
+        BATCH_TRY(b, cudaGetLastError());
+    }
+    return LBM_OK;
+}
+
+// One call in the current mode, as a CUDA graph of that call length (captured on first
+// use, replayed afterwards), or launched directly where capture is refused.
+static int run_call(lbm_batch* b, int nsteps)
+{
+    const bool per_step = b->mode == LBM_BATCH_PER_STEP;
+    bool& ok = per_step ? b->graph_ok_step : b->graph_ok;
+    auto enqueue = [&](cudaStream_t st) {
+        return per_step ? enqueue_per_step(b, nsteps, st) : enqueue_persistent(b, nsteps, st);
+    };
+    if (ok && (b->exec == nullptr || b->graph_steps != nsteps || b->graph_mode != b->mode)) {
         drop_graph(b);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
         int rc = LBM_OK;
         if (e == cudaSuccess) {
-            rc = enqueue_persistent(b, nsteps, b->capture);
+            rc = enqueue(b->capture);
             e = cudaStreamEndCapture(b->capture, &graph);
         }
         if (rc != LBM_OK && e == cudaSuccess) {
@@ -245,37 +282,20 @@ static int run_persistent(lbm_batch* b, int nsteps)
         if (e == cudaSuccess && rc == LBM_OK) e = cudaGraphInstantiate(&b->exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess || rc != LBM_OK) {
-            // capture of a cooperative launch refused: run the launches directly
+            // capture refused (e.g. of a cooperative launch): run the launches directly
             cudaGetLastError();
             b->exec = nullptr;
-            b->graph_ok = false;
+            ok = false;
         } else {
             b->graph_steps = nsteps;
+            b->graph_mode = b->mode;
         }
     }
-    if (b->graph_ok) {
+    if (ok) {
         BATCH_TRY(b, cudaGraphLaunch(b->exec, b->stream));
         return LBM_OK;
     }
-    return enqueue_persistent(b, nsteps, b->stream);
-}
-
-static int run_per_step(lbm_batch* b, int nsteps)
-{
-    for (int s = 0; s < nsteps; ++s)
-        for (int g = 0; g < NKIND; ++g) {
-            if (b->group_tiles[g] == 0) continue;
-            const BatchTable T = group_table(b, g);
-            const int kind = KIND_TILE[g];
-            cudaError_t e = dispatch(b->N, b->precision, [&](auto n, auto pr) {
-                return launch_batch_step<decltype(n)::value, decltype(pr)>(T, kind, s, b->stream);
-            });
-            if (e != cudaSuccess) return bcuda(b, e, "batch step launch");
-        }
-    if (nsteps & 1)
-        for (int g = 0; g < NKIND; ++g)
-            BATCH_TRY(b, cudaMemsetAsync(b->d_parity + g, b->parity[g] ^ 1, 1, b->stream));
-    return LBM_OK;
+    return enqueue(b->stream);
 }
 
 // One call of nsteps steps (nsteps <= INT_MAX) with the current plan.
@@ -285,7 +305,7 @@ static int batch_advance(lbm_batch* b, int nsteps)
     if (resync_cases(b))
         BATCH_TRY(b, cudaMemcpyAsync(b->d_cases, b->cases.data(), b->ncases * sizeof(BatchCase),
                                      cudaMemcpyHostToDevice, b->stream));
-    const int rc = b->mode == LBM_BATCH_PER_STEP ? run_per_step(b, nsteps) : run_persistent(b, nsteps);
+    const int rc = run_call(b, nsteps);
     if (rc != LBM_OK) return rc;
     for (int g = 0; g < NKIND; ++g) b->parity[g] ^= (unsigned char)(nsteps & 1);
     for (int c = 0; c < b->ncases; ++c) {
@@ -306,7 +326,7 @@ static lbm_batch_plan current_plan(const lbm_batch* b)
         p.tile[k][0] = KIND_TX[b->class_kind[k]];
         p.tile[k][1] = KIND_TY[b->class_kind[k]];
     }
-    p.graph = b->mode == LBM_BATCH_PERSISTENT && b->graph_ok ? 1 : 0;
+    p.graph = (b->mode == LBM_BATCH_PERSISTENT ? b->graph_ok : b->graph_ok_step) ? 1 : 0;
     return p;
 }
 

@@ -2,9 +2,10 @@
 of lbm_step, so every case of a batch must match the same case stepped alone (FP64: to
 rounding, since the batch kernels are other instantiations of the same source), and
 one case through the batch must match the CPU oracle to the 1e-10 parity bar.  Both
-launch forms, all three tile shapes, odd step counts (the persistent launch flips its
-own parity and is replayed as a captured graph), members stepped alone between batch
-steps, and the autotuner's restoration of the state are covered."""
+launch forms, all three tile shapes, odd step counts in both forms (each call is replayed
+as a captured graph; the persistent launch flips its own parity, the per-step form ends an
+odd call with a parity-flip kernel), members stepped alone between batch steps, and the
+autotuner's restoration of the state are covered."""
 import numpy as np
 import pytest
 
@@ -77,11 +78,12 @@ def test_batch_case_against_oracle(lbm):
         s.close()
 
 
-def test_batch_odd_calls_graph_replay_and_member_steps(lbm):
+@pytest.mark.parametrize("mode", ["persistent", "per_step"])
+def test_batch_odd_calls_graph_replay_and_member_steps(lbm, mode):
     cases = W.small_batch()
     ref = singles(lbm, cases, 9)
     solvers = [lbm.Solver(c).set_fields() for c in cases]
-    b = lbm.Batch(solvers)
+    b = lbm.Batch(solvers).set_plan(mode=mode, tiles=[(32, 8)] * lbm.BATCH_CLASSES)
     b.step(3).step(3)            # second call replays the captured graph; parity flips twice
     solvers[2].step(1)           # a member stepped on its own between batch calls
     b.step(1)
@@ -98,7 +100,10 @@ def test_batch_odd_calls_graph_replay_and_member_steps(lbm):
     for s, c, R in zip(solvers, cases, ref):
         e = max_err(s.fields_numpy(), R)
         assert e <= 1e-12, (c.name, e)
-    print(b.plan.as_dict())
+    plan = b.plan.as_dict()
+    print(mode, plan)
+    if mode == "per_step":
+        assert plan["graph"]       # the per-step calls replay a captured graph
     b.close()
     for s in solvers:
         s.close()
