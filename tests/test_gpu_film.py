@@ -1,0 +1,67 @@
+"""The film-freezing problem (Section 4.1) at its full size on the GPU: 16 x 256, x
+periodic, cold bottom wall T_w = -1, outflow top, Ste = 0.1, rho_s / rho_l = 0.9,
+5000 steps.  On every policy that claims the parity bar (FP64, double words) the solid
+front is within the paper's 5 % of the Neumann solution and the film height changes by
+s (1 - rho_s / rho_l), as the oracle's pins require of the oracle; the FP32 and FP16
+storage policies put the front within 0.5 lattice units of the FP64 one."""
+import numpy as np
+import pytest
+
+from paper_2603_22902_gb300 import workloads as W
+from tests._analytic import neumann_front
+
+pytestmark = pytest.mark.gpu
+
+RR, STE, STEPS = 0.9, 0.1, 5000
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for the gpu tests")
+    from paper_2603_22902_gb300 import build as B
+    B.build()
+    from paper_2603_22902_gb300 import lbm as L
+    return L
+
+
+def front(F, below=64):
+    """Solid thickness from the wall: sum of f_s phi_1 over the rows below `below`."""
+    return float(((1 - F["fl"]) * F["phi"][0])[:below].sum(axis=0).mean())
+
+
+def run(L, prec):
+    c = W.film(nx=16, ny=256, rho_ratio=RR, ste=STE)
+    s = L.Solver(c, precision=prec).set_fields()
+    h0 = float(s.fields_numpy()["phi"][0].sum(axis=0).mean())
+    s.step(STEPS)
+    F = s.fields_numpy()
+    d = s.diagnostics()
+    s.close()
+    assert d["nonfinite"] == 0
+    return F, h0
+
+
+@pytest.fixture(scope="module")
+def runs(lbm):
+    return {p: run(lbm, p) for p in ("fp64", "df64", "fp32", "fp16s")}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_film_front_and_volume_change(runs, prec):
+    F, h0 = runs[prec]
+    s = front(F)
+    h = float(F["phi"][0].sum(axis=0).mean())
+    s_ex = neumann_front(STE, 0.1 / RR, STEPS)
+    print(prec, "front", s, "Neumann", s_ex, "height change", h - h0, "expected", s * (1 - RR))
+    assert abs(s / s_ex - 1.0) < 0.05
+    assert abs((h - h0) - s * (1 - RR)) < 0.2
+
+
+@pytest.mark.parametrize("prec", ["df64", "fp32", "fp16s"])
+def test_film_front_against_fp64(runs, prec):
+    s64 = front(runs["fp64"][0])
+    s = front(runs[prec][0])
+    print(prec, "front", s, "fp64", s64)
+    assert abs(s - s64) <= 0.5
