@@ -525,7 +525,7 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--compare", default="fp16s,df64",
                     help="comma-separated policies timed beside fp64 ('none' to skip)")
-    ap.add_argument("--front-steps", type=int, default=15000)
+    ap.add_argument("--front-steps", type=int, default=20000)
     ap.add_argument("--batch-chunk", type=int, default=10, help="steps per batch call (batch_sweep_256)")
     ap.add_argument("--batch-fp64", action="store_true", help="run the batch sweep in FP64")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")

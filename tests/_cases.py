@@ -6,8 +6,12 @@ from paper_2603_22902_gb300 import workloads as W
 
 
 def sensitive_cases():
-    return {"sessile_60deg_48x40": W.sessile_drop(n=48, R=14.0, theta=60.0, ny=40),
-            "sessile_90deg_70x44": W.sessile_drop(n=70, R=20.0, theta=90.0, ny=44)}
+    # Mobility 0.02: at the single-droplet problem's 0.03 the 60-degree drop amplifies
+    # rounding in the gas below the top wall ~150-fold between steps 100 and 150 (the
+    # oracle against itself, one temperature perturbed by 2^-46), which a fixed bar at
+    # step 150 would measure instead of the kernels.
+    return {"sessile_60deg_48x40": W.sessile_drop(n=48, R=14.0, theta=60.0, ny=40, mobility=0.02),
+            "sessile_90deg_70x44": W.sessile_drop(n=70, R=20.0, theta=90.0, ny=44, mobility=0.02)}
 
 
 def small_cases():
