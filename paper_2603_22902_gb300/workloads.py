@@ -190,9 +190,13 @@ def sessile_drop(n=512, R=100.0, ste=0.1, rho_ratio=0.9, theta=90.0, T_wall=-1.0
 
 def compound_drop(n=1024, R_core=80.0, R_shell=160.0, ste=0.2, seed=3, noise=1e-3,
                   T_wall=-1.0, T0=1.0, sigma12=1e-3, sigma23=1.5e-3, sigma13=3e-3,
-                  eps=4.0, mobility=0.02, ny=None) -> Case:
+                  eps=4.0, mobility=0.03, ny=None) -> Case:
     """Encapsulated compound drop (Section 4.3, Table 3): liquid core (phase 1) inside a
-    liquid shell (phase 2) on a cold wall in gas (phase 3)."""
+    liquid shell (phase 2) on a cold wall in gas (phase 3).
+
+    The mobility is 0.03, as in the single-droplet problem: at 0.02 the 1024 x 1024 run
+    diverges before step 10 000 (FP64) or 17 500 (FP32), at 0.03 and 0.05 it stays bounded
+    through 50 000 steps (peak velocity ~2e-2)."""
     nx, ny = n, (ny or n)
     X, Y = grid(nx, ny)
     r = np.sqrt((X - nx / 2.0) ** 2 + Y ** 2)

@@ -17,7 +17,8 @@ def sensitive_cases():
 def small_cases():
     film = W.film(nx=16, ny=256)
     drop = W.perturbed(W.periodic_drop(n=37, R=9.0, rho_gas=0.2, sigma=2e-3, ny=29), seed=1, amp_u=1e-3)
-    comp = W.compound_drop(n=44, R_core=8.0, R_shell=15.0, ny=36, noise=1e-3)
+    # the parity fixtures keep the mobility they were set up with
+    comp = W.compound_drop(n=44, R_core=8.0, R_shell=15.0, ny=36, noise=1e-3, mobility=0.02)
     pool = W.lateral_pool(n=33)
     quad = W.periodic_drop(n=30, R=7.0, N=4, rho_gas=0.5, sigma=1e-3)
     quad.phi[2] = 0.3 * quad.phi[1]
