@@ -173,3 +173,25 @@ def test_batch_rejects_mixed_members(lbm):
     b.close()
     for s in (a, c, d):
         s.close()
+
+
+def test_batch_sweep_full_run(lbm):
+    # the 256-drop sweep (sides 128-512, seed 4) for its 10 000 steps in FP16 storage,
+    # one autotuned batch: every case stays finite with a bounded velocity
+    cases = W.batch_sweep()
+    solvers = [lbm.Solver(c, precision="fp16s").set_fields() for c in cases]
+    b = lbm.Batch(solvers)
+    b.autotune(trial_steps=10)
+    b.step(10000 - solvers[0].steps)
+    b.sync()
+    umax = []
+    for s in solvers:
+        assert s.steps == 10000
+        assert s.diagnostics()["nonfinite"] == 0, s.case.name
+        F = s.fields_numpy()
+        umax.append(float(np.hypot(F["ux"], F["uy"]).max()))
+    b.close()
+    for s in solvers:
+        s.close()
+    print("sweep 10000 steps: peak |u| median", float(np.median(umax)), "max", max(umax))
+    assert max(umax) < 0.05
