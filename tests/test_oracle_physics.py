@@ -115,3 +115,30 @@ def test_table1_final_height(rr):
     hf = F["phi"][0].sum(axis=0).mean()
     assert abs(hf / h0 / analytic - 1.0) < 0.015
     assert abs(hf / h0 / paper_numeric - 1.0) < 0.05     # the paper's own 5 % level
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("rr", [0.7, 0.75, 0.8, 0.85])
+def test_table1_large_expansion_rows(rr):
+    # The rows with the largest volume change.  At mobility 0.02 the films with
+    # rho_s / rho_l <= 0.8 diverge within the first 1000 steps (the start-up freezing at
+    # the wall drives the volume source faster than the phase field relaxes); Section 4.1
+    # gives no mobility, and at 0.05 every row runs.  The whole film freezes by step
+    # 16 000.  The paper's own level is 5 % on h_f / h_0 (Table 1).  The expansion h_f - h_0
+    # comes out ~1 / h_0 short of the mass-conserving h_0 (rho_l / rho_s - 1) at every row
+    # (6.4 % at h_0 = 16, 3.2 % at h_0 = 32): the volume source phi_p mdot of the phase
+    # equations gives the gas its share of the expansion in the cells of the diffuse top
+    # interface.  Bounded here by 10 %.
+    tab = _table1()
+    row = tab[np.argmin(np.abs(tab[:, 0] - rr))]
+    analytic, paper_numeric = row[1], row[2]
+    assert abs(analytic - 1.0 / rr) < 1e-4
+    c = W.film(nx=4, ny=48, h0=16.0, ste=0.1, rho_ratio=rr, mobility=0.05)
+    o = oracle.Oracle(c)
+    h0 = o.fields()["phi"][0].sum(axis=0).mean()
+    F = o.step(16000).fields()
+    assert np.isfinite(F["phi"]).all()
+    assert (F["fl"] * F["phi"][0]).sum(axis=0).mean() < 1e-6       # no liquid left
+    hf = F["phi"][0].sum(axis=0).mean()
+    assert abs(hf / h0 / paper_numeric - 1.0) < 0.05
+    assert abs((hf / h0 - 1.0) / (analytic - 1.0) - 1.0) < 0.10
