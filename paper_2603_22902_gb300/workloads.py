@@ -241,6 +241,25 @@ def periodic_drop(n=64, R=16.0, sigma=1e-3, rho_ratio=1.0, mu=0.1, eps=4.0, mobi
                 eps=eps, mobility=mobility, phi=np.stack(phis), meta=dict(R=R, sigma=sigma))
 
 
+def liquid_lens(nx=64, ny=48, R=10.0, y_bot=12.0, y_top=30.0, s12=1e-2, s23=1e-2, s13=1e-2, mu=0.1,
+                eps=4.0, mobility=0.03) -> Case:
+    """A lens of phase 2 at a flat interface between phase 1 (a band y_bot < y < y_top)
+    and phase 3, fully periodic, equal densities, no phase change: a triple junction,
+    whose interfacial angles the balance of the three tensions fixes (Section 2; with
+    equal tensions all three are 120 degrees, as in the three-phase pool of Section 4.2).
+    The lens starts as a disc of radius R centred on the upper 1-3 interface."""
+    c = periodic_drop(n=nx, ny=ny, R=R, sigma=s12, mu=mu, eps=eps, mobility=mobility, N=3)
+    c.sigma = sigma_matrix(3, {(0, 1): s12, (1, 2): s23, (0, 2): s13})
+    X, Y = grid(nx, ny)
+    lens = tanh_step(R - np.sqrt((X - nx / 2.0) ** 2 + (Y - y_top) ** 2), eps)
+    band = tanh_step(Y - y_bot, eps) * tanh_step(y_top - Y, eps)
+    phi1 = (1.0 - lens) * band
+    c.phi = np.stack([phi1, lens, 1.0 - phi1 - lens])
+    c.name = f"liquid_lens_{nx}x{ny}"
+    c.meta = dict(R=R, y_bot=y_bot, y_top=y_top, s12=s12, s23=s23, s13=s13)
+    return c
+
+
 def flat_interface(nx=4, ny=64, h0=None, sigma=1e-3, eps=4.0, mobility=0.02) -> Case:
     """Two flat interfaces in a periodic column (an exact tanh equilibrium of the AC equation)."""
     X, Y = grid(nx, ny)

@@ -1,0 +1,61 @@
+"""Interface equilibria on the GPU, held to the oracle pins' bounds: a lens of phase 2
+on a flat 1-3 interface relaxes to the angles of the tension balance (Section 2), and a
+drop on a wetting wall relaxes to its contact angle (the wetting ghost of the order
+parameter), each within 3 degrees after 6000 steps, on the FP64, double-word and FP32
+policies."""
+import pytest
+
+from paper_2603_22902_gb300 import workloads as W
+from tests._analytic import cap_angle, fit_circle, level_crossings, neumann_triangle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for the gpu tests")
+    from paper_2603_22902_gb300 import build as B
+    B.build()
+    from paper_2603_22902_gb300 import lbm as L
+    return L
+
+
+def run(L, case, prec, steps=6000):
+    s = L.Solver(case, precision=prec).set_fields()
+    s.step(steps)
+    F = s.fields_numpy()
+    d = s.diagnostics()
+    s.close()
+    assert d["nonfinite"] == 0
+    return F
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+@pytest.mark.parametrize("s12,s23,s13", [(1e-2, 1e-2, 1e-2), (1e-2, 0.7e-2, 1.2e-2)])
+def test_lens_junction_angles(lbm, prec, s12, s23, s13):
+    case = W.liquid_lens(s12=s12, s23=s23, s13=s13)
+    F = run(lbm, case, prec)
+    col = [[v] for v in F["phi"][0][:, 0]]
+    y0 = [p[1] for p in level_crossings(col) if abs(p[1] - case.meta["y_top"]) < 8.0][0]
+    pts = level_crossings(F["phi"][1])
+    _, yu, Ru = fit_circle([p for p in pts if p[1] > y0 + 3.0])
+    _, yd, Rd = fit_circle([p for p in pts if p[1] < y0 - 3.0])
+    up, dn = cap_angle(yu, Ru, y0, up=True), cap_angle(yd, Rd, y0, up=False)
+    eu, ed = neumann_triangle(s12, s23, s13)
+    print(prec, "lens arcs", up, dn, "balance", eu, ed)
+    assert abs(up - eu) < 3.0 and abs(dn - ed) < 3.0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+@pytest.mark.parametrize("theta", [60.0, 120.0])
+def test_wetting_angle(lbm, prec, theta):
+    case = W.sessile_cap(72, 36, 12.0, theta=90.0, T_wall=1.0, T0=1.0, rho_gas=1.0, mu_l=0.1,
+                         mu_gas=0.1, cp_gas=1.0, lam_gas=0.1, sigma=1e-2)
+    case.wet_cos = W.wetting(2, {W.YMIN: {(0, 1): theta}})
+    F = run(lbm, case, prec)
+    _, yc, R = fit_circle([p for p in level_crossings(F["phi"][0]) if p[1] > 3.0])
+    got = cap_angle(yc, R, 0.0, up=True)
+    print(prec, "wetting", theta, got)
+    assert abs(got - theta) < 3.0

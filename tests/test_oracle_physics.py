@@ -15,7 +15,7 @@ import pytest
 
 import oracle
 from paper_2603_22902_gb300 import workloads as W
-from tests._analytic import neumann_front, neumann_kappa
+from tests._analytic import cap_angle, fit_circle, level_crossings, neumann_front, neumann_kappa, neumann_triangle
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -142,3 +142,48 @@ def test_table1_large_expansion_rows(rr):
     hf = F["phi"][0].sum(axis=0).mean()
     assert abs(hf / h0 / paper_numeric - 1.0) < 0.05
     assert abs((hf / h0 - 1.0) / (analytic - 1.0) - 1.0) < 0.10
+
+
+def _lens_angles(F, case):
+    """Angles of the lens's upper and lower arcs with the flat 1-3 interface: circles
+    fitted to the phi_2 = 1/2 crossings more than 3 lu above / below that interface,
+    whose height is the phi_1 = 1/2 crossing in the outermost column."""
+    col = [[v] for v in F["phi"][0][:, 0]]
+    y0 = [p[1] for p in level_crossings(col) if abs(p[1] - case.meta["y_top"]) < 8.0][0]
+    pts = level_crossings(F["phi"][1])
+    xu, yu, Ru = fit_circle([p for p in pts if p[1] > y0 + 3.0])
+    xd, yd, Rd = fit_circle([p for p in pts if p[1] < y0 - 3.0])
+    return cap_angle(yu, Ru, y0, up=True), cap_angle(yd, Rd, y0, up=False)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("s12,s23,s13", [(1e-2, 1e-2, 1e-2), (1e-2, 0.7e-2, 1.2e-2)])
+def test_lens_junction_angles(s12, s23, s13):
+    # A lens of phase 2 on a flat 1-3 interface, started as a disc (both arcs at 90
+    # degrees): after 6000 steps the arcs meet the interface at the angles of the
+    # tension balance (Section 2; 60 + 60 degrees, i.e. 120-degree interfacial angles,
+    # for equal tensions, as Section 4.2 states for its three-phase pool), within 3 degrees.
+    # Unequal tensions make the two arcs differ, so a swapped pair of sigma_pq fails.
+    case = W.liquid_lens(s12=s12, s23=s23, s13=s13)
+    F = oracle.Oracle(case).step(6000).fields()
+    up, dn = _lens_angles(F, case)
+    eu, ed = neumann_triangle(s12, s23, s13)
+    print("lens arcs", up, dn, "balance", eu, ed)
+    assert abs(up - eu) < 3.0 and abs(dn - ed) < 3.0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("theta", [60.0, 120.0])
+def test_wetting_angle(theta):
+    # A drop started as a half disc (90 degrees) on a wall that wets at theta relaxes
+    # to a circular cap meeting the wall at theta (the wetting ghost of the order
+    # parameter), within 3 degrees after 6000 steps.  No phase change (T > T_m), equal
+    # densities and viscosities.  A sign error in the wetting term gives 180 - theta.
+    case = W.sessile_cap(72, 36, 12.0, theta=90.0, T_wall=1.0, T0=1.0, rho_gas=1.0, mu_l=0.1,
+                         mu_gas=0.1, cp_gas=1.0, lam_gas=0.1, sigma=1e-2)
+    case.wet_cos = W.wetting(2, {W.YMIN: {(0, 1): theta}})
+    F = oracle.Oracle(case).step(6000).fields()
+    xc, yc, R = fit_circle([p for p in level_crossings(F["phi"][0]) if p[1] > 3.0])
+    got = cap_angle(yc, R, 0.0, up=True)
+    print("wetting", theta, got)
+    assert abs(got - theta) < 3.0
