@@ -47,14 +47,34 @@ def test_flat_interface_is_stationary():
     assert abs(heights[0] - 16.0) < 1e-6 and abs(heights[1] - 48.0) < 1e-6
 
 
+def _laplace_ratio(eps, n=64, R=16.0, sigma=1e-3):
+    """Delta p R / sigma of a drop in a periodic box: the mean pressure inside r < R/2
+    minus the mean outside r > R + 2 eps, averaged over 20 samples 100 steps apart after
+    2000 steps.  Gas density 0.1 and viscosity 0.3 damp the drop's start-up oscillation
+    (the pressure starts at 0), so that the average is steady to ~1e-3."""
+    c = W.periodic_drop(n=n, R=R, sigma=sigma, rho_gas=0.1, mu=0.3, eps=eps)
+    o = oracle.Oracle(c)
+    o.step(2000)
+    X, Y = W.grid(n, n)
+    r = np.hypot(X - n / 2.0, Y - n / 2.0)
+    vals = []
+    for _ in range(20):
+        p = o.step(100).fields()["p"]
+        vals.append((p[r < R / 2].mean() - p[r > R + 2 * eps].mean()) * R / sigma)
+    return float(np.mean(vals))
+
+
 @pytest.mark.slow
-@pytest.mark.parametrize("R", [10.0, 14.0])
-def test_laplace_law(R):
-    sigma = 1e-3
-    c = W.periodic_drop(n=48, R=R, sigma=sigma, rho_gas=1.0, mu=0.1)
-    F = oracle.Oracle(c).step(3000).fields()
-    dp = F["p"][24, 24] - F["p"][0, 0]
-    assert abs(dp * R / sigma - 1.0) < 0.03
+def test_laplace_law():
+    # Delta p = sigma / R in 2D.  The chemical potential and surface force reach it as
+    # the interface is resolved: at eps = 8 lattice units within 3 %; at eps = 4 (the
+    # paper's width) the pressure jump is ~7 % low, and that error is at least 3 times
+    # the eps = 8 one (it falls as (dx / eps)^2).
+    r8, r4 = _laplace_ratio(8.0), _laplace_ratio(4.0)
+    print("Laplace dp R / sigma: eps 8", r8, "eps 4", r4)
+    assert abs(r8 - 1.0) < 0.03
+    assert abs(r4 - 1.0) >= 3.0 * abs(r8 - 1.0)
+    assert abs(r4 - 1.0) < 0.10
 
 
 def test_dirichlet_wall_conduction_erfc():
