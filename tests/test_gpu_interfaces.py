@@ -2,7 +2,8 @@
 on a flat 1-3 interface relaxes to the angles of the tension balance (Section 2), and a
 drop on a wetting wall relaxes to its contact angle (the wetting ghost of the order
 parameter), each within 3 degrees after 6000 steps, on the FP64, double-word and FP32
-policies."""
+policies; the Laplace pressure jump of large drops; and the per-phase volume change of
+a frozen two-liquid pool converging with the lattice size."""
 import pytest
 
 from paper_2603_22902_gb300 import workloads as W
@@ -87,3 +88,32 @@ def test_laplace_law_large_drops(lbm, R):
     assert abs(out[8.0] - 1.0) < 0.03
     assert abs(out[4.0] - 1.0) >= 3.0 * abs(out[8.0] - 1.0)
     assert abs(out[4.0] - 1.0) < 0.10
+
+
+def test_pool_volume_change_converges(lbm):
+    # The two-liquid pool (Section 4.2, Fig. 4) frozen through at sides 32, 64 and 128:
+    # the part of each liquid's volume change rho_l / rho_s - 1 that its phase field does
+    # not take (the share given to the other phases of its interface cells) halves with
+    # each doubling of the size, and is below 5 % at 128; a liquid with rho_s = rho_l
+    # changes by a vanishing amount likewise.
+    short, leak = [], []
+    for n, steps in ((32, 9000), (64, 36000), (128, 144000)):
+        res = {}
+        for r1, r2 in ((1.05, 0.95), (1.1, 1.0)):
+            case = W.lateral_pool(n=n, rho_ratio1=r1, rho_ratio2=r2)
+            s = lbm.Solver(case).set_fields()
+            F0 = s.fields_numpy()
+            V0 = [F0["phi"][p].sum() for p in range(2)]
+            s.step(steps)
+            F = s.fields_numpy()
+            s.close()
+            assert (F["fl"] * (F["phi"][0] + F["phi"][1])).sum() < 1e-3
+            res[(r1, r2)] = [F["phi"][p].sum() / V0[p] - 1.0 for p in range(2)]
+        a = res[(1.05, 0.95)]
+        short.append(max(1.0 - a[0] / (1 / 1.05 - 1), 1.0 - a[1] / (1 / 0.95 - 1)))
+        leak.append(abs(res[(1.1, 1.0)][1]))
+    print("pool shortfall", short, "leak", leak)
+    for k in range(2):
+        assert 1.7 < short[k] / short[k + 1] < 2.3
+        assert 1.7 < leak[k] / leak[k + 1] < 2.3
+    assert 0.0 < short[2] < 0.05

@@ -215,3 +215,26 @@ def test_wetting_angle(theta):
     got = cap_angle(yc, R, 0.0, up=True)
     print("wetting", theta, got)
     assert abs(got - theta) < 3.0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("r1,r2", [(1.05, 0.95), (1.1, 1.0)])
+def test_pool_volume_change_per_phase(r1, r2):
+    # Two liquids side by side under gas (Section 4.2, Fig. 4), frozen through from the
+    # bottom wall (32 x 32, 9000 steps).  Each liquid's volume changes by
+    # rho_l / rho_s - 1: contraction for rho_s > rho_l, expansion for rho_s < rho_l, none
+    # for rho_s = rho_l.  The phase-field source phi_p mdot shares a liquid's change with
+    # the other phases present in its interface cells, so at this size 83-88 % of the
+    # change reaches the liquid itself (the shortfall falls as 1 / size) and a liquid with
+    # rho_s = rho_l changes by ~0.5 %.
+    c = W.lateral_pool(n=32, rho_ratio1=r1, rho_ratio2=r2)
+    o = oracle.Oracle(c)
+    V0 = [o.fields()["phi"][p].sum() for p in range(2)]
+    F = o.step(9000).fields()
+    assert (F["fl"] * (F["phi"][0] + F["phi"][1])).sum() < 1e-4        # frozen through
+    for p, r in enumerate((r1, r2)):
+        dV = F["phi"][p].sum() / V0[p] - 1.0
+        if r == 1.0:
+            assert abs(dV) < 0.1 * abs(1.0 / r1 - 1.0), (p, dV)
+        else:
+            assert 0.75 < dV / (1.0 / r - 1.0) <= 1.0, (p, dV)
