@@ -73,3 +73,51 @@ def test_total_momentum_conserved(lbm, prec):
     print(prec, "momentum drift", rel)
     assert np.abs(F1["ux"] - F0["ux"]).max() > 1e-5
     assert rel <= BOUND[prec]
+
+
+def _with_absent_phase(c2):
+    """The same case with a third phase that is absent everywhere (phi_3 = 0)."""
+    import numpy as np
+    c3 = c2.copy()
+    c3.N = 3
+    c3.phi = np.concatenate([c2.phi, np.zeros((1, c2.ny, c2.nx))])
+    c3.phases = c2.phases + [W.phase(rho_l=0.5, rho_s=0.4, latent=3.0)]
+    s = np.zeros((3, 3))
+    s[:2, :2] = c2.sigma
+    s[0, 2] = s[2, 0] = 2e-3
+    s[1, 2] = s[2, 1] = 1e-3
+    c3.sigma = s
+    wc = np.zeros((4, 3, 3))
+    wc[:, :2, :2] = c2.wet_cos
+    c3.wet_cos = wc
+    return c3
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("df64", 1e-10), ("fp32", 1e-4)])
+@pytest.mark.parametrize("name", ["film_16x256", "periodic_drop_37x29"])
+def test_absent_phase_reduction(lbm, prec, tol, name):
+    # Reduction consistency (Section 2): an N = 3 run whose third phase is absent is the
+    # N = 2 run.  Every term of the absent phase is an exact zero (4 phi_p phi_3 / eps,
+    # g'(phi_p + 0) - g'(phi_p), its equilibria and sources), so phi_3 stays exactly 0;
+    # the N = 2 and N = 3 kernels are separate instantiations whose multiply-adds the
+    # compiler may contract differently, so the other fields agree to the policy's
+    # rounding after 1000 steps: FP64 to ~1e-13 (bound 1e-11), double words to ~1e-11
+    # (bound: their parity bar against the oracle, 1e-10), FP32 to ~2e-5 in T (bound 1e-4,
+    # inside the FP32 policy's bounds against the oracle).
+    import numpy as np
+    from tests._cases import small_cases
+    c2 = small_cases()[name]
+    c3 = _with_absent_phase(c2)
+    out = []
+    for c in (c2, c3):
+        s = lbm.Solver(c, precision=prec).set_fields()
+        s.step(1000)
+        out.append(s.fields_numpy())
+        s.close()
+    F2, F3 = out
+    assert np.all(F3["phi"][2] == 0.0)
+    errs = {k: float(np.abs(F2[k] - F3[k]).max()) for k in ("T", "H", "fl", "ux", "uy", "p")}
+    errs["phi"] = float(np.abs(F2["phi"] - F3["phi"][:2]).max())
+    print(prec, name, errs)
+    for k, v in errs.items():
+        assert v <= tol, (k, v)
