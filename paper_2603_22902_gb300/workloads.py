@@ -260,6 +260,21 @@ def liquid_lens(nx=64, ny=48, R=10.0, y_bot=12.0, y_top=30.0, s12=1e-2, s23=1e-2
     return c
 
 
+def channel(T0=1.0, H=32, g=1e-6, mu=0.1, nx=4) -> Case:
+    """A liquid filling a channel between walls at y = 0 and y = H (half-way bounce-back),
+    x periodic, driven by a body force g along x; walls and fluid at temperature T0
+    (T0 > T_m: liquid, T0 < T_m: frozen solid with rho_s = rho_l)."""
+    c = Case(name=f"channel_{nx}x{H}", nx=nx, ny=H, N=2,
+             phases=[phase(rho_l=1.0, rho_s=1.0, mu_l=mu, latent=latent_from_stefan(0.1)),
+                     phase(rho_l=1.0, mu_l=mu)],
+             sigma=sigma_matrix(2, {(0, 1): 1e-3}),
+             bc=(PERIODIC, PERIODIC, WALL, WALL), tbc=(ADIABATIC, ADIABATIC, DIRICHLET, DIRICHLET),
+             T_wall=(0.0, 0.0, T0, T0), accel=(g, 0.0),
+             phi=np.stack([np.ones((H, nx)), np.zeros((H, nx))]), T=np.full((H, nx), T0),
+             meta=dict(g=g, mu=mu))
+    return c
+
+
 def flat_interface(nx=4, ny=64, h0=None, sigma=1e-3, eps=4.0, mobility=0.02) -> Case:
     """Two flat interfaces in a periodic column (an exact tanh equilibrium of the AC equation)."""
     X, Y = grid(nx, ny)

@@ -117,3 +117,20 @@ def test_pool_volume_change_converges(lbm):
         assert 1.7 < short[k] / short[k + 1] < 2.3
         assert 1.7 < leak[k] / leak[k + 1] < 2.3
     assert 0.0 < short[2] < 0.05
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+def test_poiseuille_and_frozen_channel(lbm, prec):
+    # The oracle pin's channel on the GPU: the liquid's steady profile within 2e-3 of
+    # Poiseuille's peak, and the same channel frozen held below 1e-3 of it by the penalty
+    import numpy as np
+    H, g, mu = 32, 1e-6, 0.1
+    y = np.arange(H) + 0.5
+    exact = g / (2.0 * mu) * y * (H - y)
+    F = run(lbm, W.channel(1.0, H, g, mu), prec, steps=40000)
+    print(prec, "poiseuille rel err", float(np.abs(F["ux"] - exact[:, None]).max() / exact.max()))
+    assert np.abs(F["ux"] - exact[:, None]).max() < 2e-3 * exact.max()
+    F = run(lbm, W.channel(-1.0, H, g, mu), prec, steps=40000)
+    print(prec, "frozen channel umax", float(np.abs(F["ux"]).max()))
+    assert F["fl"].max() == 0.0
+    assert np.abs(F["ux"]).max() < 1e-3 * exact.max()

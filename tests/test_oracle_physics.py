@@ -240,22 +240,6 @@ def test_pool_volume_change_per_phase(r1, r2):
             assert 0.75 < dV / (1.0 / r - 1.0) <= 1.0, (p, dV)
 
 
-def _channel(T0, H=32, g=1e-6, mu=0.1):
-    """A liquid filling a channel between walls at y = 0 and y = H (half-way bounce-back),
-    x periodic, driven by a body force g along x; walls and fluid at temperature T0
-    (T0 > T_m: liquid; T0 < T_m: frozen solid, rho_s = rho_l)."""
-    c = W.flat_interface(nx=4, ny=H)
-    c.phi = np.stack([np.ones((H, 4)), np.zeros((H, 4))])
-    c.phases = [W.phase(rho_l=1.0, rho_s=1.0, mu_l=mu, latent=W.latent_from_stefan(0.1)),
-                W.phase(rho_l=1.0, mu_l=mu)]
-    c.bc = (W.PERIODIC, W.PERIODIC, W.WALL, W.WALL)
-    c.tbc = (W.ADIABATIC, W.ADIABATIC, W.DIRICHLET, W.DIRICHLET)
-    c.T_wall = (0.0, 0.0, T0, T0)
-    c.T = np.full((H, 4), T0)
-    c.accel = (g, 0.0)
-    return c
-
-
 @pytest.mark.slow
 def test_poiseuille_and_frozen_channel():
     # Liquid: the steady profile is u(y) = g y (H - y) / (2 nu) (the flow LBE's viscosity
@@ -266,9 +250,9 @@ def test_poiseuille_and_frozen_channel():
     H, g, mu = 32, 1e-6, 0.1
     y = np.arange(H) + 0.5
     exact = g / (2.0 * mu) * y * (H - y)
-    F = oracle.Oracle(_channel(1.0, H, g, mu)).step(40000).fields()
+    F = oracle.Oracle(W.channel(1.0, H, g, mu)).step(40000).fields()
     assert np.abs(F["ux"] - exact[:, None]).max() < 2e-3 * exact.max()
     assert np.abs(F["uy"]).max() < 1e-12
-    F = oracle.Oracle(_channel(-1.0, H, g, mu)).step(40000).fields()
+    F = oracle.Oracle(W.channel(-1.0, H, g, mu)).step(40000).fields()
     assert F["fl"].max() == 0.0
     assert np.abs(F["ux"]).max() < 1e-3 * exact.max()
