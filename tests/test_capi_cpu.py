@@ -52,6 +52,8 @@ def _create(case, **mods):
 
 @pytest.mark.parametrize("mods", [
     dict(grid__nx=2),
+    dict(grid__ny=2),
+    dict(grid__nx=65536, grid__ny=40000),   # more than 2^31 cells
     dict(num__eps=0.0),
     dict(num__mobility=-1.0),
     dict(num__precision=7),
@@ -67,6 +69,16 @@ def test_invalid_parameters_rejected(lib, mods):
     case = W.film(nx=8, ny=16)
     with pytest.raises(lbm.LBMError) as e:
         _create(case, **mods)
+    assert e.value.code == lbm.LBM_EINVAL
+
+
+@pytest.mark.parametrize("N", [1, 5])
+def test_phase_count_out_of_range_rejected(lib, N):
+    case = W.film(nx=8, ny=16)
+    grid, phases, th, bc, num = lbm.make_structs(case)
+    phases = (list(phases) * N)[:N]
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_create(grid, N, phases, th, bc, num)
     assert e.value.code == lbm.LBM_EINVAL
 
 
