@@ -75,3 +75,20 @@ def cap_angle(yc: float, R: float, y0: float, up: bool = True) -> float:
     or below it."""
     c = (y0 - yc) / R if up else (yc - y0) / R
     return math.degrees(math.acos(max(-1.0, min(1.0, c))))
+
+
+def neumann_kappa_superheated(ste: float, superheat: float) -> float:
+    """Root of Ste / (exp(k^2) erf(k)) - superheat Ste / (exp(k^2) erfc(k)) = k sqrt(pi):
+    the two-phase Neumann problem (Section 4.1 transcendental equation) with equal
+    conductivities, diffusivities and densities in the solid and the liquid, and
+    superheat = (T_0 - T_m) / (T_m - T_w)."""
+    f = lambda k: (ste / (math.exp(k * k) * math.erf(k)) - superheat * ste / (math.exp(k * k) * math.erfc(k))
+                   - k * math.sqrt(math.pi))
+    lo, hi = 1e-9, 3.0
+    for _ in range(200):                      # f decreases from +inf
+        mid = 0.5 * (lo + hi)
+        if f(mid) > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)

@@ -15,7 +15,8 @@ import pytest
 
 import oracle
 from paper_2603_22902_gb300 import workloads as W
-from tests._analytic import cap_angle, fit_circle, level_crossings, neumann_front, neumann_kappa, neumann_triangle
+from tests._analytic import (cap_angle, fit_circle, level_crossings, neumann_front, neumann_kappa,
+                             neumann_kappa_superheated, neumann_triangle)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -25,6 +26,18 @@ def test_neumann_kappa_small_stefan_series():
     for ste in (1e-4, 1e-3, 1e-2):
         k = neumann_kappa(ste)
         assert abs(2 * k * k * (1 + 2 * k * k / 3) - ste) < 2 * ste ** 3
+
+
+def test_neumann_kappa_superheated_limits():
+    # no superheat: the one-phase root; superheat slows the front
+    for ste in (0.05, 0.1, 0.5):
+        assert abs(neumann_kappa_superheated(ste, 0.0) - neumann_kappa(ste)) < 1e-14
+        ks = [neumann_kappa_superheated(ste, sh) for sh in (0.0, 0.5, 1.0, 2.0)]
+        assert all(a > b for a, b in zip(ks, ks[1:]))
+    # small k: erfc(k) -> 1, exp(k^2) erf(k) -> 2 k / sqrt(pi), so the balance reads
+    # Ste sqrt(pi) / (2 k) - superheat Ste = k sqrt(pi) + O(k Ste): k -> sqrt(Ste / 2)
+    for ste in (1e-6, 1e-8):
+        assert abs(neumann_kappa_superheated(ste, 1.0) / math.sqrt(ste / 2.0) - 1.0) < 10 * math.sqrt(ste)
 
 
 def test_flat_interface_is_stationary():
@@ -101,6 +114,19 @@ def test_neumann_front_without_density_change():
     F = oracle.Oracle(c).step(5000).fields()
     s = _front(F, 128)
     s_ex = neumann_front(0.1, 0.1 / 1.0, 5000)
+    assert abs(s / s_ex - 1.0) < 0.03
+
+
+@pytest.mark.slow
+def test_neumann_front_superheated_liquid():
+    # The liquid starts at T_0 = 1 above T_m = 0 (the paper's film setting, Section 4.1):
+    # the two-phase Neumann solution with equal solid and liquid properties, kappa =
+    # 0.1891 against 0.2200 without superheat.  The gas above the film has the liquid's
+    # rho c_p and lambda, so the medium is thermally uniform.  Within 3 % at 5000 steps.
+    c = W.film(nx=4, ny=256, rho_ratio=1.0, ste=0.1, T0=1.0)
+    F = oracle.Oracle(c).step(5000).fields()
+    s = _front(F, 128)
+    s_ex = 2.0 * neumann_kappa_superheated(0.1, 1.0) * math.sqrt(0.1 * 5000)
     assert abs(s / s_ex - 1.0) < 0.03
 
 
