@@ -90,3 +90,21 @@ def test_table1_rows_frozen_through(lbm, prec, rr):
     print(prec, rr, "h_f/h_0", hf / h0, "paper", row[2], "analytic", row[1])
     assert abs(hf / h0 / row[2] - 1.0) < 0.05
     assert abs((hf / h0 - 1.0) / (row[1] - 1.0) - 1.0) < 0.10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+def test_superheated_film_front(lbm, prec):
+    # The film with the liquid at T_0 = 1 above T_m (the paper's film setting), rho_s =
+    # rho_l: the front follows the two-phase Neumann solution within 3 % at 5000 steps,
+    # as the oracle pin requires of the oracle
+    import math
+    from tests._analytic import neumann_kappa_superheated
+    c = W.film(nx=16, ny=256, rho_ratio=1.0, ste=0.1, T0=1.0)
+    s = lbm.Solver(c, precision=prec).set_fields()
+    s.step(5000)
+    F = s.fields_numpy()
+    s.close()
+    sf = front(F, 128)
+    s_ex = 2.0 * neumann_kappa_superheated(0.1, 1.0) * math.sqrt(0.1 * 5000)
+    print(prec, "superheated front", sf, "Neumann", s_ex)
+    assert abs(sf / s_ex - 1.0) < 0.03
