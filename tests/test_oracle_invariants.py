@@ -98,10 +98,12 @@ def test_total_enthalpy_conserved_without_phase_change(rho_gas):
     assert abs(E1 - E0) <= 1e-12 * float(np.abs(F0["H"] * F0["rho"]).sum()), (E0, E1)
 
 
-def test_sum_of_order_parameters_exact_without_flow():
-    c = W.periodic_drop(n=24, R=6.0, N=3, sigma=0.0)
-    c.phi[2] = 0.5 * c.phi[1]
-    c.phi[1] = 0.5 * c.phi[1]
+@pytest.mark.parametrize("N", [3, 4])
+def test_sum_of_order_parameters_exact_without_flow(N):
+    c = W.periodic_drop(n=24, R=6.0, N=N, sigma=0.0)
+    share = c.phi[1] / (N - 1)
+    for p in range(1, N):
+        c.phi[p] = share
     c.bc = (W.WALL, W.WALL, W.WALL, W.WALL)
     o = oracle.Oracle(c).step(300)
     F = o.fields()
@@ -131,6 +133,30 @@ def test_absent_phase_reduction_is_exact():
     assert np.array_equal(F2["phi"], F3["phi"][:2])
     g3 = o3.populations()[1][2]
     assert np.all(g3 == 0.0)
+
+
+def test_absent_fourth_phase_reduction_is_exact():
+    # the same with N = 3 -> 4: the three-phase pool freezing under gas, plus an absent
+    # fourth phase with its own tensions and latent heat
+    c3 = W.lateral_pool(n=24, rho_ratio1=1.05, rho_ratio2=0.95)
+    c4 = c3.copy()
+    c4.N = 4
+    c4.phi = np.concatenate([c3.phi, np.zeros((1, c3.ny, c3.nx))])
+    c4.phases = c3.phases + [W.phase(rho_l=0.7, rho_s=0.6, latent=2.0)]
+    s = np.full((4, 4), 1.5e-3)
+    np.fill_diagonal(s, 0.0)
+    s[:3, :3] = c3.sigma
+    c4.sigma = s
+    wc = np.zeros((4, 4, 4))
+    wc[:, :3, :3] = c3.wet_cos
+    c4.wet_cos = wc
+    o3, o4 = oracle.Oracle(c3).step(150), oracle.Oracle(c4).step(150)
+    F3, F4 = o3.fields(), o4.fields()
+    assert np.all(F4["phi"][3] == 0.0)
+    for k in ("T", "H", "fl", "ux", "uy", "p", "rho"):
+        assert np.array_equal(F3[k], F4[k]), k
+    assert np.array_equal(F3["phi"], F4["phi"][:3])
+    assert np.all(o4.populations()[1][3] == 0.0)
 
 
 def test_two_phase_reduces_to_textbook_model():
