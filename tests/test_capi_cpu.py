@@ -106,3 +106,23 @@ def test_batch_arguments_rejected_before_any_cuda_call(lib):
 
 def test_adjoint_arguments_rejected_before_any_cuda_call(lib):
     assert lib.lbm_adjoint_fl_loss(None, None, None, None, None, None, None, 0, 1, 1, None) == lbm.LBM_EINVAL
+
+
+def test_no_device_fails_loudly(lib):
+    # without a CUDA device a valid parameter set is refused with LBM_ECUDA: there is no
+    # CPU path behind the C ABI
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    case = W.film(nx=8, ny=16)
+    with pytest.raises(lbm.LBMError) as e:
+        _create(case)
+    assert e.value.code == lbm.LBM_ECUDA
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    # the binding never falls back to anything when the built library is absent
+    monkeypatch.setattr(lbm, "_lib", None)
+    monkeypatch.setattr(lbm, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "liblbm_gb300.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        lbm.library()
