@@ -378,15 +378,17 @@ def compare_precision(case, precisions, mlups_fp64, front_steps, stream, flush):
     """Other policies against FP64 on the same GPU: throughput timed like the headline,
     and the freezing-front position after front_steps steps from the same initial state."""
     from paper_2603_22902_gb300 import lbm
-    from paper_2603_22902_gb300.metrics import front_height
+    from paper_2603_22902_gb300.metrics import front_height, front_integral
     hbm_peak, _ = load_peaks()
     out = {}
-    fronts = {}
+    fronts, integrals = {}, {}
     for prec in ["fp64"] + list(precisions):
         if front_steps > 0:
             s = lbm.Solver(case, precision=prec).set_fields()
             s.step(front_steps)
-            fronts[prec] = front_height(s.fields_numpy(), case.nx)
+            F = s.fields_numpy()
+            fronts[prec] = front_height(F, case.nx)
+            integrals[prec] = front_integral(F, case.nx)
             s.close()
         if prec == "fp64":
             continue
@@ -397,7 +399,9 @@ def compare_precision(case, precisions, mlups_fp64, front_steps, stream, flush):
              "hbm_frac": round(bpl * mlups * 1e6 / 1e9 / hbm_peak, 4)}
         if front_steps > 0:
             r.update({"front_steps": front_steps, "front_fp64_lu": round(fronts["fp64"], 4),
-                      "front_err_lu": float(f"{abs(fronts[prec] - fronts['fp64']):.3g}"), "front_err_bound_lu": 0.5})
+                      "front_err_lu": float(f"{abs(fronts[prec] - fronts['fp64']):.3g}"), "front_err_bound_lu": 0.5,
+                      "front_integral_fp64_lu": round(integrals["fp64"], 4),
+                      "front_integral_err_lu": float(f"{abs(integrals[prec] - integrals['fp64']):.3g}")})
         counts = ncu_counts(prec, case.N)
         if counts:
             wi = counts["warp_inst"] * mlups * 1e6 / 1e9
