@@ -22,6 +22,13 @@
  * A primed quantity (') is the value stored by the previous step.
  * The readings of passages the paper leaves open are listed in the design notes;
  * the ones that change arithmetic are named where they are used below.
+ *
+ * Parity unpinned (no test ties these to anything but the code itself):
+ *   - the wetting ghost of the order parameters for N > 2 at contact angles other
+ *     than 90 degrees (the paper defers that boundary condition to another work);
+ *   - the penalty force's weighting chi = f_s * sum of the phase-changing phi_p in
+ *     cells that also hold ambient fluid (in cells of phase-changing material alone
+ *     it is the paper's f_s and is pinned by the frozen channel).
  */
 #include "lbo.h"
 
