@@ -25,7 +25,8 @@
  *
  * Parity unpinned (no test ties these to anything but the code itself):
  *   - the wetting ghost of the order parameters for N > 2 at contact angles other
- *     than 90 degrees (the paper defers that boundary condition to another work);
+ *     than 90 degrees (the paper defers that boundary condition to another work;
+ *     only its exact reduction to the N = 2 law with a phase absent is tested);
  *   - the penalty force's weighting chi = f_s * sum of the phase-changing phi_p in
  *     cells that also hold ambient fluid (in cells of phase-changing material alone
  *     it is the paper's f_s and is pinned by the frozen channel).

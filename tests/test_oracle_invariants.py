@@ -124,6 +124,11 @@ def test_absent_phase_reduction_is_exact():
     c3.sigma = s
     wc = np.zeros((4, 3, 3))
     wc[:, :2, :2] = c2.wet_cos
+    # the absent phase wets the wall at its own angles: its ghost terms carry phi_3 = 0
+    # as a factor, so the pairwise wetting ghost reduces to the N = 2 law exactly
+    for p, ang in ((0, 50.0), (1, 110.0)):
+        wc[W.YMIN, p, 2] = np.cos(np.radians(ang))
+        wc[W.YMIN, 2, p] = -wc[W.YMIN, p, 2]
     c3.wet_cos = wc
     o2, o3 = oracle.Oracle(c2).step(150), oracle.Oracle(c3).step(150)
     F2, F3 = o2.fields(), o3.fields()
