@@ -202,3 +202,31 @@ def test_rotation_symmetry():
     assert np.abs(np.rot90(Fa["p"]) - Fb["p"]).max() < 1e-15
     assert np.abs(np.rot90(Fa["uy"]) - Fb["ux"]).max() < 1e-15
     assert np.abs(np.rot90(-Fa["ux"]) - Fb["uy"]).max() < 1e-15
+
+
+def _periodic_centroid(phi):
+    """Centroid of phi on a periodic lattice, from the first Fourier mode of each axis."""
+    ny, nx = phi.shape
+    out = []
+    for prof, n in ((phi.sum(0), nx), (phi.sum(1), ny)):
+        th = 2.0 * np.pi * (np.arange(n) + 0.5) / n
+        out.append(np.angle((prof * np.exp(1j * th)).sum()) % (2.0 * np.pi) * n / (2.0 * np.pi))
+    return out
+
+
+def test_uniform_translation_with_equal_densities():
+    # Galilean invariance: a drop of the gas's density carried by a uniform velocity
+    # u0 moves by u0 t and keeps that velocity (advection in the phase-field equilibria
+    # and the flow equilibria).  A dropped c_i . u term in g_eq leaves the drop behind.
+    n, u0, steps = 48, (0.02, 0.01), 1000
+    c = W.periodic_drop(n=n, R=10.0, sigma=1e-3, rho_gas=1.0, mu=0.1)
+    c.ux = np.full((n, n), u0[0])
+    c.uy = np.full((n, n), u0[1])
+    o = oracle.Oracle(c)
+    x0 = _periodic_centroid(o.fields()["phi"][0])
+    F = o.step(steps).fields()
+    x1 = _periodic_centroid(F["phi"][0])
+    for a, b, u in zip(x0, x1, u0):
+        d = (b - a + n / 2) % n - n / 2
+        assert abs(d / (u * steps) - 1.0) < 1e-3, (d, u * steps)
+    assert abs(F["ux"].mean() / u0[0] - 1.0) < 1e-3 and abs(F["uy"].mean() / u0[1] - 1.0) < 1e-3
