@@ -134,3 +134,22 @@ def test_poiseuille_and_frozen_channel(lbm, prec):
     print(prec, "frozen channel umax", float(np.abs(F["ux"]).max()))
     assert F["fl"].max() == 0.0
     assert np.abs(F["ux"]).max() < 1e-3 * exact.max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+def test_uniform_translation_with_equal_densities(lbm, prec):
+    # the oracle pin's translating drop: displacement u0 t within 1e-3, velocity kept
+    import numpy as np
+    from tests.test_oracle_invariants import _periodic_centroid
+    n, u0, steps = 48, (0.02, 0.01), 1000
+    case = W.periodic_drop(n=n, R=10.0, sigma=1e-3, rho_gas=1.0, mu=0.1)
+    case.ux = np.full((n, n), u0[0])
+    case.uy = np.full((n, n), u0[1])
+    x0 = _periodic_centroid(case.phi[0])
+    F = run(lbm, case, prec, steps=steps)
+    x1 = _periodic_centroid(F["phi"][0])
+    for a, b, u in zip(x0, x1, u0):
+        d = (b - a + n / 2) % n - n / 2
+        print(prec, "translation", d, u * steps)
+        assert abs(d / (u * steps) - 1.0) < 1e-3
+    assert abs(F["ux"].mean() / u0[0] - 1.0) < 1e-3 and abs(F["uy"].mean() / u0[1] - 1.0) < 1e-3
