@@ -34,3 +34,29 @@ def test_oracle_does_not_use_the_product():
             text = fh.read()
         assert not pat.search(text), p
         assert "import paper_2603_22902_gb300" not in text and "from paper_2603_22902_gb300" not in text, p
+
+
+def _functions_importing_oracle(path):
+    import ast
+    with open(path) as fh:
+        tree = ast.parse(fh.read())
+    found = []
+
+    def visit(node, func):
+        for child in ast.iter_child_nodes(node):
+            name = child.name if isinstance(child, (ast.FunctionDef, ast.AsyncFunctionDef)) else func
+            if isinstance(child, ast.Import) and any(a.name.split(".")[0] == "oracle" for a in child.names):
+                found.append(func)
+            if isinstance(child, ast.ImportFrom) and (child.module or "").split(".")[0] == "oracle":
+                found.append(func)
+            visit(child, name)
+
+    visit(tree, None)
+    return found
+
+
+def test_bench_and_entry_use_the_oracle_only_where_allowed():
+    # bench.py: only the CPU-baseline / reference timing; __graft_entry__: smoke() checks
+    # against it, build() compiles it (building the checker is not using it)
+    assert _functions_importing_oracle(os.path.join(ROOT, "bench.py")) == ["time_oracle"]
+    assert set(_functions_importing_oracle(os.path.join(ROOT, "__graft_entry__.py"))) <= {"build", "smoke"}
