@@ -135,7 +135,8 @@ typedef struct {
 int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_thermal* thermal,
                const lbm_bc* bc, const lbm_numerics* numerics, lbm_handle** out);
 
-/* Queue all later work of the handle on `stream` (a cudaStream_t; NULL = default). */
+/* Queue all later work of the handle on `stream` (a cudaStream_t; NULL = default).
+ * A service of the library: the paper has no counterpart. */
 int lbm_set_stream(lbm_handle* h, void* stream);
 
 /* Initial state at t = 0 from phi [N][ny][nx], T, ux, uy (ux / uy may be NULL = 0):
@@ -156,10 +157,19 @@ int lbm_step(lbm_handle* h, long nsteps);
 int lbm_get_fields(lbm_handle* h, double* phi, double* T, double* H, double* fl, double* ux,
                    double* uy, double* p, int where);
 
-/* Diagnostics of the current state (synchronises the handle's stream). */
+/* Diagnostics of the current state (synchronises the handle's stream): the quantities
+ * behind the paper's conservation claims, measured on the lattice.  Per-phase volume
+ * sum_x phi_p: conserved to round-off without phase change (the conservative Allen-Cahn
+ * LBE of Section 3 with the source phi_p mdot, Section 2; mass conservation of the
+ * N-phase model stated in the Conclusions), and its change on freezing the volume change
+ * of Section 4.1 (Table 1: h_f / h_0 = rho_l / rho_s).  Per-phase solid volume
+ * sum_x f_s phi_p: the frozen amount (eq. H, f_s = 1 - f_l).  max_x |sum_p phi_p - 1|: the
+ * constraint sum_p phi_p = 1 that the pairwise R_p keeps (Section 2, reduction
+ * consistency).  Non-finite count: a cell whose sum_p phi_p, rho H or f_0 is not finite. */
 int lbm_get_diagnostics(lbm_handle* h, lbm_diag* out);
 
-/* Raw state: *bytes receives the size of the checkpoint; buf may be NULL to query.
+/* Raw state (a service of the library for checkpoint and restart; the paper has no
+ * counterpart): *bytes receives the size of the checkpoint; buf may be NULL to query.
  * lbm_save_state copies populations, lagged planes and the step counter to host
  * memory; lbm_load_state restores them on a handle created with the same grid, N and
  * precision. */
@@ -190,7 +200,9 @@ int lbm_set_tile(lbm_handle* h, int bx, int by);
  * fraction fl [ny][nx] (as written by lbm_get_fields with LBM_DEVICE); out is a
  * caller-owned device array of 2N + 2 doubles that receives, as lbm_get_diagnostics does,
  * sum_x phi_p (N values), sum_x (1 - fl) phi_p (N values), max_x |sum_p phi_p - 1| and the
- * count of non-finite cells.  The work is queued on `stream` (a cudaStream_t, NULL = the
+ * count of non-finite cells.  That count looks only at the fields passed in: a cell counts
+ * when fl or sum_p phi_p is not finite (lbm_get_diagnostics also looks at rho H and the rest
+ * population of f, which are not inputs here).  The work is queued on `stream` (a cudaStream_t, NULL = the
  * default stream) and the call returns without synchronising.
  * The block partial sums live in a fixed array of 608 x 10 doubles (48.6 KiB) in the
  * library's device image, which every GPU that loads the library holds until the process
@@ -200,13 +212,17 @@ int lbm_set_tile(lbm_handle* h, int bx, int by);
  * device looks up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  All calls share the array, so
  * calls whose work overlaps on the GPU (other streams, other host threads) race; calls
- * on one stream are ordered and safe.  No cudaMalloc, cudaFree or allocating library
- * routine is called. */
+ * on one stream are ordered and safe.  The looked-up address holds for the life of the
+ * device's primary context: do not use this call across a cudaDeviceReset.  A CUDA error
+ * already pending from earlier work makes the call return LBM_ECUDA without launching
+ * (the error is left pending for its owner).  No cudaMalloc, cudaFree or allocating
+ * library routine is called. */
 int lbm_field_sums_noalloc(const double* phi, const double* fl, int nx, int ny, int N, double* out,
                            void* stream);
 
-/* Message of the last failing call on h (or of the last failing lbm_create when
- * h is NULL).  Never NULL. */
+/* Message of the last failing call on h.  With h = NULL: the message of the calling
+ * thread's last failing call that has no handle (lbm_create, lbm_field_sums_noalloc);
+ * each host thread keeps its own.  Never NULL. */
 const char* lbm_last_error(const lbm_handle* h);
 
 void lbm_destroy(lbm_handle* h);
@@ -300,6 +316,15 @@ int lbm_batch_get_plan(const lbm_batch* b, lbm_batch_plan* plan);
  *   after 2^21 polls (about a second; more for groups above 16M cells), and the next
  *   lbm_batch_sync reports LBM_ETIMEOUT. */
 int lbm_batch_step(lbm_batch* b, long nsteps);
+
+/* Bound of every grid-barrier wait of the persistent form, in polls (0 = the default:
+ * 2^21 polls, or one per 8 cells of the largest group).  A service for tests of the
+ * timeout path and for callers that want a step to fail fast rather than wait about a
+ * second: with a bound of a few polls the first wait gives up, every block of the launch
+ * leaves at its next barrier, the state of the cases is left partly stepped (undefined)
+ * and the next lbm_batch_sync returns LBM_ETIMEOUT and resets the barrier.  Waits for the
+ * batch's queued work first.  polls < 0 is LBM_EINVAL. */
+int lbm_batch_set_wait_limit(lbm_batch* b, long long polls);
 
 /* Wait for the batch's queued work. Returns LBM_OK, LBM_ETIMEOUT (a grid-barrier wait
  * gave up; the barrier is reset) or LBM_ECUDA. */

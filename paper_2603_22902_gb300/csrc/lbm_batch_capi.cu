@@ -50,6 +50,7 @@ struct lbm_batch {
     std::vector<lbm_handle*> h;
     int mode = LBM_BATCH_PERSISTENT;
     int blocks_per_sm = 0;
+    long long wait_limit = 0;               // polls of a barrier wait; 0 = the size-based default
     int class_kind[LBM_BATCH_CLASSES] = {0, 0, 0, 0};
     // tables: host mirrors and device copies
     std::vector<BatchCase> cases;
@@ -173,7 +174,7 @@ static BatchTable group_table(const lbm_batch* b, int g)
     T.parity = b->d_parity + g;
     T.bar = b->d_bar + 2 * g;
     T.status = b->d_status;
-    T.spin_limit = std::max(SPIN_MIN, b->group_cells[g] / 8);
+    T.spin_limit = b->wait_limit > 0 ? b->wait_limit : std::max(SPIN_MIN, b->group_cells[g] / 8);
     return T;
 }
 
@@ -429,6 +430,17 @@ int lbm_batch_set_stream(lbm_batch* b, void* stream)
 {
     if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
     b->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+int lbm_batch_set_wait_limit(lbm_batch* b, long long polls)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
+    if (polls < 0) return bfail(b, LBM_EINVAL, "polls must be >= 0");
+    BATCH_TRY(b, cudaSetDevice(b->device));
+    BATCH_TRY(b, cudaStreamSynchronize(b->stream));
+    b->wait_limit = polls;
+    drop_graph(b);  // the limit is a kernel argument captured in the graph
     return LBM_OK;
 }
 

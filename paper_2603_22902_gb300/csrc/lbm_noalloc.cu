@@ -31,7 +31,10 @@ constexpr int NA_MAX_DEVICES = 64;
 static __device__ __align__(256) double g_noalloc_partial[NA_MAX_BLOCKS * NA_MAX_K];
 
 // Device addresses of g_noalloc_partial, looked up once per device with that device
-// current (the host-side symbol is only a stand-in, not a device address).
+// current (the host-side symbol is only a stand-in, not a device address).  They stay
+// valid for the life of the device's primary context: after cudaDeviceReset the module
+// is loaded again and the cached address may be stale, so this entry point must not be
+// used across a reset.
 double* g_scratch_addr[NA_MAX_DEVICES] = {};
 std::mutex g_scratch_mutex;
 
@@ -111,6 +114,12 @@ extern "C" int lbm_field_sums_noalloc(const double* phi, const double* fl, int n
         set_handle_free_error("lbm_field_sums_noalloc: nx * ny exceeds 2^31 cells");
         return LBM_EINVAL;
     }
+    // an error left pending by earlier, unrelated work is reported as such and left in
+    // place, not taken over as a failure of this call's launches
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        set_handle_free_error("lbm_field_sums_noalloc: a CUDA error from earlier work is pending; nothing launched");
+        return LBM_ECUDA;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
         cudaGetLastError();
@@ -135,9 +144,13 @@ extern "C" int lbm_field_sums_noalloc(const double* phi, const double* fl, int n
     if (nb > NA_MAX_BLOCKS) nb = NA_MAX_BLOCKS;  // grid-stride: the scratch never holds more rows
     cudaStream_t st = (cudaStream_t)stream;
     na_partial<<<(int)nb, NA_THREADS, 0, st>>>(phi, fl, cells, N, scratch);
+    if (cudaGetLastError() != cudaSuccess) {  // no second pass over rows that were not written
+        set_handle_free_error("lbm_field_sums_noalloc: launch of the partial-sum kernel failed");
+        return LBM_ECUDA;
+    }
     na_final<<<1, 32, 0, st>>>(scratch, (int)nb, N, out);
     if (cudaGetLastError() != cudaSuccess) {
-        set_handle_free_error("lbm_field_sums_noalloc: kernel launch failed");
+        set_handle_free_error("lbm_field_sums_noalloc: launch of the final-sum kernel failed");
         return LBM_ECUDA;
     }
     return LBM_OK;

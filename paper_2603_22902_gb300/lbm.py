@@ -121,6 +121,7 @@ def library():
             lib.lbm_batch_get_plan.argtypes = [_VP, P(lbm_batch_plan)]
             lib.lbm_batch_step.argtypes = [_VP, ctypes.c_long]
             lib.lbm_batch_sync.argtypes = [_VP]
+            lib.lbm_batch_set_wait_limit.argtypes = [_VP, ctypes.c_longlong]
             lib.lbm_batch_autotune.argtypes = [_VP, ctypes.c_int, P(lbm_batch_plan)]
             lib.lbm_batch_last_error.argtypes = [_VP]
             lib.lbm_batch_last_error.restype = ctypes.c_char_p
@@ -128,7 +129,7 @@ def library():
             for name in ("lbm_create", "lbm_set_stream", "lbm_set_fields", "lbm_step", "lbm_get_fields",
                          "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile",
                          "lbm_batch_create", "lbm_batch_set_stream", "lbm_batch_set_plan", "lbm_batch_get_plan",
-                         "lbm_batch_step", "lbm_batch_sync", "lbm_batch_autotune", "lbm_adjoint_fl_loss"):
+                         "lbm_batch_step", "lbm_batch_sync", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_adjoint_fl_loss"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -263,6 +264,10 @@ def lbm_batch_step(b, nsteps):
 
 def lbm_batch_sync(b):
     return _bcheck(library().lbm_batch_sync(b), b)
+
+
+def lbm_batch_set_wait_limit(b, polls):
+    return _bcheck(library().lbm_batch_set_wait_limit(b, int(polls)), b)
 
 
 def lbm_batch_autotune(b, trial_steps):
@@ -410,6 +415,10 @@ class Batch:
 
     def sync(self):
         lbm_batch_sync(self.b)
+        return self
+
+    def set_wait_limit(self, polls):
+        lbm_batch_set_wait_limit(self.b, polls)
         return self
 
     def autotune(self, trial_steps=20):

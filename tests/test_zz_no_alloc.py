@@ -69,3 +69,49 @@ def test_noalloc_rejects_sizes_beyond_its_limits(lbm):
     rc = lib.lbm_field_sums_noalloc(a.data_ptr(), a.data_ptr(), 1 << 16, 1 << 16, 2, a.data_ptr(), None)
     assert rc == lbm.LBM_EINVAL
     assert b"2^31" in lib.lbm_last_error(None)
+
+
+def test_noalloc_sums_on_a_lattice_beyond_one_row_per_block(lbm):
+    # 512 x 512 = 262 144 cells: more than 608 blocks x 256 threads, so the grid-stride
+    # loop folds several cells into each of the fixed 608 scratch rows
+    import torch
+    lib = lbm.library()
+    case = W.sessile_drop()
+    N = case.N
+    assert case.nx * case.ny > 608 * 256
+    s = lbm.Solver(case).set_fields()
+    s.step(40)
+    F = s.fields()
+    stream = torch.cuda.current_stream().cuda_stream
+    out = torch.full((2 * N + 2,), float("nan"), dtype=torch.float64, device="cuda")
+    rc = lib.lbm_field_sums_noalloc(F["phi"].data_ptr(), F["fl"].data_ptr(), case.nx, case.ny, N,
+                                    out.data_ptr(), stream)
+    assert rc == lbm.LBM_OK, lib.lbm_last_error(None)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    d = s.diagnostics()
+    for p in range(N):
+        assert abs(got[p] - d["mass"][p]) <= 1e-10 * abs(d["mass"][p]), p
+        assert abs(got[N + p] - d["solid"][p]) <= 1e-10 * max(1.0, abs(d["solid"][p])), p
+    assert abs(got[2 * N] - d["max_sum_dev"]) <= 1e-10
+    assert got[2 * N + 1] == 0.0
+    s.close()
+
+
+def test_noalloc_counts_a_nonfinite_cell_of_its_inputs(lbm):
+    import torch
+    lib = lbm.library()
+    case = W.sessile_drop(n=96, R=28.0, ny=80, theta=70.0)
+    N = case.N
+    s = lbm.Solver(case).set_fields()
+    s.step(20)
+    F = s.fields()
+    phi = F["phi"].clone()
+    phi[1, 33, 47] = float("nan")
+    out = torch.zeros(2 * N + 2, dtype=torch.float64, device="cuda")
+    rc = lib.lbm_field_sums_noalloc(phi.data_ptr(), F["fl"].data_ptr(), case.nx, case.ny, N, out.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream)
+    assert rc == lbm.LBM_OK, lib.lbm_last_error(None)
+    torch.cuda.synchronize()
+    assert out[2 * N + 1].item() == 1.0
+    s.close()
