@@ -227,6 +227,59 @@ const char* lbm_last_error(const lbm_handle* h);
 
 void lbm_destroy(lbm_handle* h);
 
+/* ---- y slabs: one lattice as bands of rows, one handle per band -------------------------
+ * The fused step (Section 3) is a one-cell stencil in every field, so a lattice cut into
+ * bands of rows steps exactly like the whole lattice when, after every step, each cut is
+ * crossed by two messages per direction:
+ *   phase 1: the populations that the step pushed across the cut (the three directions
+ *            with c_y across it, of every species: 3 (N + 2) rows of nx values);
+ *   phase 2: the boundary row's phase-field and enthalpy populations (all nine directions,
+ *            9 (N + 1) rows) and its lagged mdot' and Q' (2 rows): the inputs from which
+ *            the next step's stencil ring recomputes phi_p, rho and psi.
+ * A slab handle holds rows [y0, y1) plus one ghost row beyond each cut side; the ghost
+ * rows are stepped too, and the exchange overwrites what they get wrong.  The same calls
+ * serve two handles on one GPU (a device-to-device copy of the message) and handles on
+ * different GPUs (NCCL send / receive of the packed buffers).  The paper solves one
+ * lattice on one machine; this is a service of the library for lattices that do not fit
+ * one GPU. */
+
+/* A handle for rows [y0, y1) of the lattice `grid` with the global parameters.  A side
+ * of the band is a cut where another band continues the lattice: y0 > 0, y1 < ny, or
+ * either when the y sides are periodic.  A cut side gets a ghost row and is declared an
+ * adiabatic, neutrally wetting wall of the band's own lattice (it touches only the ghost
+ * row); the other side keeps the global boundary rule.  The band's lattice has
+ * (y1 - y0) + ghosts rows, at least 3.  lbm_set_fields takes that lattice's fields: global
+ * rows y0 - 1 .. y1 (wrapped when periodic, without the rows beyond a global side).
+ * lbm_get_fields returns them, ghost rows included; lbm_slab_sums gives the diagnostics
+ * sums over the band's own rows (lbm_get_diagnostics would count the ghost rows).  Errors
+ * as lbm_create; y0, y1 out of range or a band without a cut is LBM_EINVAL. */
+int lbm_slab_create(const lbm_grid* grid, int y0, int y1, int N, const lbm_phase* phases,
+                    const lbm_thermal* thermal, const lbm_bc* bc, const lbm_numerics* numerics,
+                    lbm_handle** out);
+
+/* out4 = {rows of the band's lattice, ghost row below (0/1), ghost row above (0/1), y0}. */
+int lbm_slab_geometry(const lbm_handle* h, int* out4);
+
+/* Bytes of one message of `phase` (1 or 2) through one cut (rows padded to 16 bytes);
+ * -1 for a handle that is not a slab or a bad phase. */
+long long lbm_slab_message_bytes(const lbm_handle* h, int phase);
+
+/* Pack the message of `phase` that the handle sends through its cut side `side` (2 = y-min,
+ * 3 = y-max) into the device buffer msg; unpack the message that arrives through that
+ * side.  Per step, in this order: lbm_step on every band; phase 1 packs of every cut, then
+ * the transfers, then phase 1 unpacks; the same for phase 2.  The message that a band
+ * packs on its y-max side is unpacked by the band above on its y-min side, and the other
+ * way round.  Queued on the handle's stream; no synchronisation.  A side that is not a cut
+ * is LBM_EINVAL. */
+int lbm_slab_pack(lbm_handle* h, int side, int phase, void* msg);
+int lbm_slab_unpack(lbm_handle* h, int side, int phase, const void* msg);
+
+/* Diagnostics sums over the band's own rows, into host memory out[2N + 2]: sum phi_p (N),
+ * sum (1 - f_l) phi_p (N), max |sum_p phi_p - 1|, and the count of cells where sum_p phi_p,
+ * f_l, T, H, u or p is not finite.  Adding the sums (and taking the maximum of the
+ * deviation) over all bands gives the lattice's diagnostics.  Synchronises the stream. */
+int lbm_slab_sums(lbm_handle* h, double* out);
+
 /* ---- gradients: the adjoint of the FP64 step -------------------------------------------
  * Loss of the liquid fraction after nsteps steps from given initial fields:
  *     L = sum_x w(x) (phi_pcm(x) f_l(x) - f_target(x))^2,  w = 1 when weight is NULL,

@@ -60,6 +60,7 @@ class Params(ctypes.Structure):
         ("T_wall", ctypes.c_double * 4),
         ("wet_cos", (ctypes.c_double * (MAXN * MAXN)) * 4),
         ("two_phase_textbook", ctypes.c_int),
+        ("penalty_literal", ctypes.c_int),
     ]
 
 
@@ -94,7 +95,7 @@ def _ptr(a):
     return a.ctypes.data_as(_DP)
 
 
-def make_params(case, two_phase_textbook: bool = False) -> Params:
+def make_params(case, two_phase_textbook: bool = False, penalty_literal: bool = False) -> Params:
     """Fill the oracle's parameter structure from a case description."""
     P = Params()
     P.nx, P.ny, P.N = case.nx, case.ny, case.N
@@ -122,17 +123,18 @@ def make_params(case, two_phase_textbook: bool = False) -> Params:
             for q in range(case.N):
                 P.wet_cos[side][p * MAXN + q] = wc[p, q]
     P.two_phase_textbook = 1 if two_phase_textbook else 0
+    P.penalty_literal = 1 if penalty_literal else 0
     return P
 
 
 class Oracle:
     """The CPU oracle on one case: ``step(n)`` then ``fields()``."""
 
-    def __init__(self, case, two_phase_textbook: bool = False):
+    def __init__(self, case, two_phase_textbook: bool = False, penalty_literal: bool = False):
         self._lib = _load()
         self.case = case
         self.N, self.nx, self.ny = case.N, case.nx, case.ny
-        self._P = make_params(case, two_phase_textbook)
+        self._P = make_params(case, two_phase_textbook, penalty_literal)
         phi = np.ascontiguousarray(case.phi, dtype=np.float64)
         T = np.ascontiguousarray(case.T, dtype=np.float64)
         ux = np.ascontiguousarray(case.ux, dtype=np.float64)

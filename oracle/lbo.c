@@ -24,12 +24,9 @@
  * the ones that change arithmetic are named where they are used below.
  *
  * Parity unpinned (no test ties these to anything but the code itself):
- *   - the wetting ghost of the order parameters for N > 2 at contact angles other
- *     than 90 degrees (the paper defers that boundary condition to another work;
- *     only its exact reduction to the N = 2 law with a phase absent is tested);
- *   - the penalty force's weighting chi = f_s * sum of the phase-changing phi_p in
- *     cells that also hold ambient fluid (in cells of phase-changing material alone
- *     it is the paper's f_s and is pinned by the frozen channel).
+ *   (none left: the pairwise wetting ghost of N > 2 is pinned by the Janus drop's
+ *   wetting lengths of Table 2, and the penalty weight in mixed cells by the frozen
+ *   layer under a driven channel of ambient fluid)
  */
 #include "lbo.h"
 
@@ -275,7 +272,9 @@ static void stage_B(lbo_state* s)
         s->lam[c] = fs * m.ks + l * m.kl;
         s->cp[c] = fs * m.cs + l * m.cl;
         s->psi[c] = fs * m.drho;
-        s->chi[c] = fs * m.pcm;
+        /* penalty weight: the solid volume fraction f_s * sum of the phase-changing phi_p
+         * (reading of the penalty force in cells that also hold ambient fluid) */
+        s->chi[c] = s->P.penalty_literal ? fs : fs * m.pcm;
     }
 }
 

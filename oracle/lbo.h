@@ -44,6 +44,9 @@ typedef struct {
     double T_wall[4];                  /* Dirichlet wall temperature per side */
     double wet_cos[4][LBO_MAXN * LBO_MAXN]; /* cos(theta_pq) per wall side, antisymmetric */
     int two_phase_textbook;            /* N = 2 only: textbook two-phase interface terms (pin) */
+    int penalty_literal;               /* pin only: penalty weight f_s instead of f_s * sum of
+                                          the phase-changing phi_p (shows that the frozen-layer
+                                          pin tells the two readings apart) */
 } lbo_params;
 
 typedef struct lbo_state lbo_state;

@@ -27,5 +27,9 @@ struct lbm_handle {
     bool ready = false;
     long long steps = 0;
     cudaStream_t stream = nullptr;
+    // y slab (lbm_slab_create): ghost rows below / above the band, first global row
+    bool slab = false;
+    int slab_ghost[2] = {0, 0};
+    int slab_y0 = 0;
     std::string err;
 };

@@ -115,6 +115,14 @@ def library():
             lib.lbm_destroy.argtypes = [_VP]
             lib.lbm_adjoint_fl_loss.argtypes = [_VP] + [_VP] * 6 + [ctypes.c_int, ctypes.c_long, ctypes.c_int,
                                                                      P(lbm_fl_grad)]
+            lib.lbm_slab_create.argtypes = [P(lbm_grid), ctypes.c_int, ctypes.c_int, ctypes.c_int, P(lbm_phase),
+                                            P(lbm_thermal), P(lbm_bc), P(lbm_numerics), P(_VP)]
+            lib.lbm_slab_geometry.argtypes = [_VP, P(ctypes.c_int)]
+            lib.lbm_slab_message_bytes.argtypes = [_VP, ctypes.c_int]
+            lib.lbm_slab_message_bytes.restype = ctypes.c_longlong
+            lib.lbm_slab_pack.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
+            lib.lbm_slab_unpack.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
+            lib.lbm_slab_sums.argtypes = [_VP, P(_D)]
             lib.lbm_batch_create.argtypes = [ctypes.c_int, P(_VP), P(_VP)]
             lib.lbm_batch_set_stream.argtypes = [_VP, _VP]
             lib.lbm_batch_set_plan.argtypes = [_VP, P(lbm_batch_plan)]
@@ -128,6 +136,7 @@ def library():
             lib.lbm_batch_destroy.argtypes = [_VP]
             for name in ("lbm_create", "lbm_set_stream", "lbm_set_fields", "lbm_step", "lbm_get_fields",
                          "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile",
+                         "lbm_slab_create", "lbm_slab_geometry", "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_sums",
                          "lbm_batch_create", "lbm_batch_set_stream", "lbm_batch_set_plan", "lbm_batch_get_plan",
                          "lbm_batch_step", "lbm_batch_sync", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_adjoint_fl_loss"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -167,6 +176,39 @@ def lbm_create(grid, N, phases, thermal, bc, numerics):
     _check(library().lbm_create(ctypes.byref(grid), N, arr, ctypes.byref(thermal), ctypes.byref(bc),
                                 ctypes.byref(numerics), ctypes.byref(h)))
     return h
+
+
+def lbm_slab_create(grid, y0, y1, N, phases, thermal, bc, numerics):
+    h = _VP()
+    arr = (lbm_phase * N)(*phases)
+    _check(library().lbm_slab_create(ctypes.byref(grid), int(y0), int(y1), N, arr, ctypes.byref(thermal),
+                                     ctypes.byref(bc), ctypes.byref(numerics), ctypes.byref(h)))
+    return h
+
+
+def lbm_slab_geometry(h):
+    out = (ctypes.c_int * 4)()
+    _check(library().lbm_slab_geometry(h, out), h)
+    return tuple(out)
+
+
+def lbm_slab_message_bytes(h, phase):
+    return int(library().lbm_slab_message_bytes(h, int(phase)))
+
+
+def lbm_slab_pack(h, side, phase, msg):
+    return _check(library().lbm_slab_pack(h, int(side), int(phase), _ptr(msg)), h)
+
+
+def lbm_slab_unpack(h, side, phase, msg):
+    return _check(library().lbm_slab_unpack(h, int(side), int(phase), _ptr(msg)), h)
+
+
+def lbm_slab_sums(h, N):
+    out = (_D * (2 * N + 2))()
+    _check(library().lbm_slab_sums(h, out), h)
+    v = list(out)
+    return dict(mass=v[:N], solid=v[N:2 * N], max_sum_dev=v[2 * N], nonfinite=int(v[2 * N + 1]))
 
 
 def lbm_set_stream(h, stream_ptr):
@@ -378,6 +420,50 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class SlabSolver(Solver):
+    """Rows [y0, y1) of a case's lattice as a slab handle (lbm_slab_create): the band plus
+    a ghost row beyond each cut side.  set_fields() takes the case's global fields and
+    hands the band's rows (ghost rows included, wrapped on a periodic axis) to the
+    library."""
+
+    def __init__(self, case, y0, y1, precision="fp64", tile=None, stream=None):
+        import torch
+        self.torch = torch
+        self.case = case
+        self.y0, self.y1 = int(y0), int(y1)
+        grid, phases, th, bc, num = make_structs(case, precision, 0)
+        self.h = lbm_slab_create(grid, self.y0, self.y1, case.N, phases, th, bc, num)
+        self.ny_local, self.ghost_below, self.ghost_above, _ = lbm_slab_geometry(self.h)
+        self.N, self.nx, self.ny = case.N, case.nx, self.ny_local
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        lbm_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream))
+        if tile is not None:
+            lbm_set_tile(self.h, *tile)
+        self.rows = np.arange(self.y0 - self.ghost_below, self.y1 + self.ghost_above) % case.ny
+        self.msg_bytes = {ph: lbm_slab_message_bytes(self.h, ph) for ph in (1, 2)}
+
+    def set_fields(self, phi=None, T=None, ux=None, uy=None):
+        c = self.case
+        r = self.rows
+        pick = lambda a, g: np.ascontiguousarray((g if a is None else a)[..., r, :])
+        return Solver.set_fields(self, pick(phi, c.phi), pick(T, c.T), pick(ux, c.ux), pick(uy, c.uy))
+
+    def own(self, F):
+        """The band's own rows of a field dict from fields() / fields_numpy()."""
+        lo, hi = self.ghost_below, self.ny_local - self.ghost_above
+        return {k: v[..., lo:hi, :] for k, v in F.items()}
+
+    def pack(self, side, phase, msg):
+        lbm_slab_pack(self.h, side, phase, msg)
+
+    def unpack(self, side, phase, msg):
+        lbm_slab_unpack(self.h, side, phase, msg)
+
+    def sums(self):
+        return lbm_slab_sums(self.h, self.N)
 
 
 class Batch:

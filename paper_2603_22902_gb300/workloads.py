@@ -275,6 +275,24 @@ def channel(T0=1.0, H=32, g=1e-6, mu=0.1, nx=4) -> Case:
     return c
 
 
+def frozen_layer_channel(H=64, h=12.0, g=1e-6, mu=0.1, T0=-0.5, nx=4, eps=4.0, sigma=1e-3,
+                         mobility=0.02) -> Case:
+    """A frozen layer of phase-changing material (phase 0, y < h, tanh profile) under a
+    channel of ambient fluid (phase 1, latent heat 0), walls at y = 0 and y = H (half-way
+    bounce-back), x periodic, driven by a body force g along x.  Walls (Dirichlet) and
+    fluid at T0 < T_m, so the layer stays solid; equal densities (also rho_s = rho_l) and
+    viscosities, so nothing changes volume and the interface stays flat."""
+    X, Y = grid(nx, H)
+    phi0 = tanh_step(h - Y, eps)
+    return Case(name=f"frozen_layer_{nx}x{H}", nx=nx, ny=H, N=2,
+                phases=[phase(rho_l=1.0, rho_s=1.0, mu_l=mu, latent=latent_from_stefan(0.1)),
+                        phase(rho_l=1.0, mu_l=mu)],
+                sigma=sigma_matrix(2, {(0, 1): sigma}), eps=eps, mobility=mobility,
+                bc=(PERIODIC, PERIODIC, WALL, WALL), tbc=(ADIABATIC, ADIABATIC, DIRICHLET, DIRICHLET),
+                T_wall=(0.0, 0.0, T0, T0), accel=(g, 0.0), phi=np.stack([phi0, 1.0 - phi0]),
+                T=np.full((H, nx), T0), meta=dict(g=g, mu=mu, h=h))
+
+
 def flat_interface(nx=4, ny=64, h0=None, sigma=1e-3, eps=4.0, mobility=0.02) -> Case:
     """Two flat interfaces in a periodic column (an exact tanh equilibrium of the AC equation)."""
     X, Y = grid(nx, ny)
@@ -336,6 +354,42 @@ def sessile_cap(nx, ny, R, theta=90.0, ste=0.1, T_wall=-1.0, T0=1.0, name=None, 
     c.name = name or f"sessile_cap_{nx}x{ny}_th{theta:.0f}"
     c.meta.update(yc=yc)
     return c
+
+
+def janus_drop(nx=300, ny=150, R=60.0, theta13=75.0, theta23=90.0, eps=5.0, sigma=0.01, mu=0.1,
+               mobility=0.05) -> Case:
+    """Janus compound drop on a flat substrate (Section 4.3, Table 2): a half disc of
+    radius R on the bottom wall, its left half liquid 1 (phase 0), its right half liquid 2
+    (phase 1), in a third fluid (phase 2), with the initial profiles of Section 4.3.
+    Equal pairwise tensions, no phase change.
+
+    Wall wetting of the bottom wall: theta13 and theta23 are the angles of liquids 1 and 2
+    against the third fluid (measured inside the liquid); the 1-2 contact line takes the
+    angle that Young's law gives with the same wall energies,
+    sigma_12 cos theta_12 = sigma_13 cos theta_13 - sigma_23 cos theta_23.  The top wall is
+    neutral (90 degrees) and x is periodic.  Proposed where the paper is silent or its
+    values do not apply here: equal densities and viscosities (without gravity the
+    equilibrium shape depends only on the tensions and the wall angles), viscosity mu,
+    mobility 0.05."""
+    X, Y = grid(nx, ny)
+    x = X - nx / 2.0
+    disc = tanh_step(R - np.sqrt(x ** 2 + Y ** 2), eps)
+    phi1 = disc * tanh_step(-x, eps)
+    phi2 = disc * tanh_step(x, eps)
+    phi = np.stack([phi1, phi2, 1.0 - phi1 - phi2])
+    c13, c23 = math.cos(math.radians(theta13)), math.cos(math.radians(theta23))
+    c12 = (sigma * c13 - sigma * c23) / sigma
+    w = np.zeros((4, 3, 3))
+    for (p, q), cv in {(0, 2): c13, (1, 2): c23, (0, 1): c12}.items():
+        w[YMIN, p, q] = cv
+        w[YMIN, q, p] = -cv
+    phases = [phase(rho_l=1.0, mu_l=mu), phase(rho_l=1.0, mu_l=mu), phase(rho_l=1.0, mu_l=mu)]
+    sig = np.full((3, 3), sigma)
+    np.fill_diagonal(sig, 0.0)
+    return Case(name=f"janus_drop_{nx}x{ny}_th{theta23:.0f}", nx=nx, ny=ny, N=3, phases=phases, sigma=sig,
+                eps=eps, mobility=mobility, bc=(PERIODIC, PERIODIC, WALL, WALL), wet_cos=w, phi=phi,
+                T=np.zeros((ny, nx)), meta=dict(R=R, theta13=theta13, theta23=theta23, theta12=math.degrees(
+                    math.acos(c12))))
 
 
 BATCH_SIDES = (128, 192, 256, 384, 512)
