@@ -97,6 +97,19 @@ def ncu_counts(precision, N):
     return None
 
 
+def case_params(case):
+    """Physical and numerical parameters of a workload, for the line's config."""
+    m = case.meta
+    out = {"eps": case.eps, "mobility": case.mobility, "T0": float(case.T.flat[0])}
+    for k in ("R", "R_core", "R_shell", "ste", "rho_ratio", "theta", "T_wall", "h0"):
+        if k in m:
+            out[k] = m[k]
+    sig = [float(case.sigma[p, q]) for p in range(case.N) for q in range(p + 1, case.N)]
+    out["sigma"] = sig if len(sig) > 1 else sig[0]
+    out["rho_l"] = [ph["rho_l"] for ph in case.phases]
+    return out
+
+
 def make_case(name):
     from paper_2603_22902_gb300 import workloads as W
     if name == "sessile_drop_512":
@@ -191,11 +204,34 @@ def barrier(world):
         dist.barrier()
 
 
-def time_oracle(case, steps, budget_s=20.0, warmup=1):
-    """The CPU oracle as it stands: oracle time steps of the case, single thread, after
-    `warmup` untimed steps; stops early when the budget is spent."""
+def host_info():
+    """CPU model and the number of cores this process may run on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    return model, cores
+
+
+def time_oracle(case, steps, budget_s=20.0, warmup=1, omp=False):
+    """The CPU oracle as it stands: oracle time steps of the case after `warmup` untimed
+    steps, one thread (or, with omp=True, its -fopenmp build on every core this process
+    may use); stops early when the budget is spent."""
     import oracle
-    o = oracle.Oracle(case)
+    o = oracle.Oracle(case, omp=omp)
     o.step(warmup)  # warm (page-in, caches)
     done, t0 = 0, time.perf_counter()
     while done < steps:
@@ -214,12 +250,15 @@ def run_reference(args):
     case = make_case(args.workload)
     mlups, done, dt = time_oracle(case, args.steps, budget_s=args.ref_budget, warmup=args.warmup)
     cores = 1
+    model, avail = host_info()
     line = {
         "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": done, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / done, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "N": case.N},
+        "data": "synthetic", "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "N": case.N,
+                                        "params": case_params(case)},
         "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "cpu_model": model, "cores_available": avail,
                          "sample": f"{done} timed oracle steps of {case.name} (of {args.steps} requested, after "
                                    f"{args.warmup} untimed; {args.ref_budget:.0f} s budget), one host thread"},
         "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -282,15 +321,24 @@ def run_gpu(args):
     gbs = bpl * mlups_rank * 1e6 / 1e9
     counts = ncu_counts(args.precision, N)
     traffic = round(counts["dram_bytes"] * cells) if counts else None
+    fp64_peak, fp64_peak_kind = FP64_PIPE_PEAK_GINST, "derived: 152 SMs x 2 FP64 lanes/clock x 2.07 GHz"
+    if args.precision == "fp64":
+        try:
+            r, ms = lbm.lbm_measure_fp64_rate()
+            fp64_peak = r
+            fp64_peak_kind = (f"measured: FP64 FMA loop (lbm_measure_fp64_rate, best of 5 launches of {ms:.2f} ms "
+                              f"after 3 untimed); derived {FP64_PIPE_PEAK_GINST:.1f}")
+        except lbm.LBMError:
+            pass
     roof_hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(gbs / hbm_peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} (copy bandwidth)", "bytes_per_lu": bpl, "lu_per_launch": cells}
     roofline = roof_hbm
     if counts and args.precision == "fp64":
         gi = counts["fp64_inst"] * mlups_rank * 1e6 / 1e9
-        roofline = {"bound": "alu", "achieved": round(gi, 1), "peak": round(FP64_PIPE_PEAK_GINST, 1),
-                    "unit": "G FP64-pipe inst/s", "frac": round(gi / FP64_PIPE_PEAK_GINST, 4), "traffic": traffic,
-                    "peak_kind": "derived: 152 SMs x 2 FP64 lanes/clock x 2.07 GHz",
+        roofline = {"bound": "alu", "achieved": round(gi, 1), "peak": round(fp64_peak, 1),
+                    "unit": "G FP64-pipe inst/s", "frac": round(gi / fp64_peak, 4), "traffic": traffic,
+                    "peak_kind": fp64_peak_kind,
                     "fp64_inst_per_lu": counts["fp64_inst"], "lu_per_launch": cells,
                     "tflops": round(counts["fp64_flop"] * mlups_rank * 1e6 / 1e12, 4),
                     "hbm": {k: roof_hbm[k] for k in ("achieved", "peak", "unit", "frac", "bytes_per_lu")}}
@@ -318,14 +366,24 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        model, avail = host_info()
         mlups_cpu, done, dt = time_oracle(case, 10 ** 6, budget_s=args.cpu_budget)
         cpu = {"value": round(mlups_cpu, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"{done} oracle time steps of {case.name} ({dt:.1f} s), one host thread"}
+               "sample": f"{done} oracle time steps of {case.name} ({dt:.1f} s), one host thread",
+               "cpu_model": model, "cores_available": avail}
+        if avail > 1:
+            mlups_omp, done_o, dt_o = time_oracle(case, 10 ** 6, budget_s=args.cpu_budget, omp=True)
+            cpu["openmp"] = {"value": round(mlups_omp, 4), "unit": "MLUPS", "cores": avail,
+                             "sample": f"{done_o} oracle time steps of {case.name} ({dt_o:.1f} s), the -fopenmp build "
+                                       f"of the same source (per-cell loops over {avail} threads)"}
 
     s.close()
     rp = None
     if world == 1 and args.precision == "fp64" and args.compare and args.compare != "none":
         rp = compare_precision(case, args.compare.split(","), mlups_rank, args.front_steps, stream, flush)
+    extra = {}
+    if world == 1 and args.precision == "fp64" and args.workload == "sessile_drop_512" and args.extras != "none":
+        extra = extra_workloads(args, lbm, stream, flush)
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
@@ -335,6 +393,7 @@ def run_gpu(args):
                       "bf16s": "bf16-storage/f32"}[args.precision],
             "data": "synthetic",
             "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "N": N, "precision": args.precision,
+                       "params": case_params(case),
                        "l2": "flushed (256 MiB write) before every timed step", "timing": "CUDA events per step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
@@ -348,6 +407,7 @@ def run_gpu(args):
             if "df64" in rp:
                 line["double_word"] = rp.pop("df64")
             line.update({f"compare_{k}": v for k, v in rp.items()})
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -417,6 +477,113 @@ def compare_precision(case, precisions, mlups_fp64, front_steps, stream, flush):
             r["traffic"] = round(counts["dram_bytes"] * case.cells)
         out[prec] = r
     return out
+
+
+def extra_workloads(args, lbm, stream, flush):
+    """The other single-GPU configurations, timed by this same run:
+    - compound_drop_1024: 1024 x 1024, N = 3, each policy timed like the headline (L2
+      flushed before every timed step, CUDA events per step);
+    - batch_sweep_256: the 256-drop sweep in one batch (FP16 storage), autotuned plan,
+      CUDA events per call of --batch-chunk steps (state far larger than L2);
+    - adjoint_impurity_512: one call of the hand-written adjoint on the 512 x 512 pool with
+      24 impurity disks (N = 4), 4000 steps, checkpoint every 200: seconds per call (CUDA
+      events on the handle's stream) and the share of a plain forward run of the same
+      length; and the loss of that run's FP64 forward beside the loss of an FP32 forward."""
+    import numpy as np
+    import torch
+    from paper_2603_22902_gb300 import workloads as W
+    hbm_peak, _ = load_peaks()
+    out = {}
+    parts = args.extras.split(",")
+    if "compound" in parts:
+        case = W.compound_drop()
+        r = {"workload": case.name, "N": case.N, "params": case_params(case), "steps": 200}
+        for prec in ("fp64", "df64", "fp32", "fp16s"):
+            mlups = timed_mlups(lbm, case, prec, 200, stream, flush)
+            bpl = bytes_per_lu(case.N, prec)
+            r[prec] = {"value": round(mlups, 2), "unit": "MLUPS", "bytes_per_lu": bpl,
+                       "hbm_frac": round(bpl * mlups * 1e6 / 1e9 / hbm_peak, 4)}
+        out["compound_drop_1024"] = r
+    if "batch" in parts:
+        out["batch_sweep_256"] = batch_measure(args, lbm, stream, steps=200, warmup=20)
+    if "adjoint" in parts:
+        from paper_2603_22902_gb300.grad import final_liquid_fraction, pcm_liquid_fraction
+        nsteps, K = 4000, 200
+        case = W.impurity_freeze(T_wall=-1.0)
+        target = final_liquid_fraction(W.impurity_freeze(T_wall=-1.3), nsteps)
+        d = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        s = lbm.Solver(case, precision="fp64")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        g = lbm.lbm_adjoint_fl_loss(s.h, d(case.phi), d(case.T), d(case.ux), d(case.uy), d(target), None,
+                                    lbm.LBM_HOST, nsteps, K)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        s.set_fields()
+        ev[2].record(stream)
+        s.step(nsteps)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        F64 = s.fields_numpy()
+        s.close()
+        t_call, t_fwd = ev[0].elapsed_time(ev[1]) * 1e-3, ev[2].elapsed_time(ev[3]) * 1e-3
+        s = lbm.Solver(case, precision="fp32").set_fields()
+        s.step(nsteps)
+        F32 = s.fields_numpy()
+        s.close()
+        loss64 = float(((pcm_liquid_fraction(case, F64) - target) ** 2).sum())
+        loss32 = float(((pcm_liquid_fraction(case, F32) - target) ** 2).sum())
+        out["adjoint_impurity_512"] = {
+            "workload": case.name, "N": case.N, "steps": nsteps, "checkpoint_every": K,
+            "seconds_per_call": round(t_call, 3), "forward_s": round(t_fwd, 3),
+            "forward_share": round(t_fwd / t_call, 4), "loss_fp64": g.loss, "loss_fp64_forward_check": loss64,
+            "loss_fp32_forward": loss32, "grad_T_wall": g.T_wall[2],
+            "timing": "CUDA events on the handle's stream around one lbm_adjoint_fl_loss call"}
+    return out
+
+
+def batch_measure(args, lbm, stream, steps, warmup):
+    """Throughput of the 256-drop sweep in one batch (FP16 storage), autotuned plan."""
+    import torch
+    from paper_2603_22902_gb300 import workloads as W
+    prec = "fp16s"
+    cases = W.batch_sweep()
+    cells = sum(c.cells for c in cases)
+    solvers = [lbm.Solver(c, precision=prec).set_fields() for c in cases]
+    batch = lbm.Batch(solvers)
+    t0 = time.perf_counter()
+    batch.autotune(trial_steps=args.batch_chunk)
+    tune_s = time.perf_counter() - t0
+    chunk = args.batch_chunk
+    calls = max(1, steps // chunk)
+    for _ in range(max(1, warmup // chunk)):
+        batch.step(chunk)
+    batch.sync()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(calls)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(calls)]
+    torch.cuda.synchronize()
+    for k in range(calls):
+        starts[k].record(stream)
+        batch.step(chunk)
+        ends[k].record(stream)
+    batch.sync()
+    t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    nonfinite = sum(s.diagnostics()["nonfinite"] for s in solvers)
+    plan = batch.plan.as_dict()
+    batch.close()
+    for s in solvers:
+        s.close()
+    if nonfinite:
+        raise SystemExit("non-finite state during the batch measurement")
+    hbm_peak, _ = load_peaks()
+    mlups = cells * calls * chunk / (t_ms * 1e-3) / 1e6
+    bpl = bytes_per_lu(2, prec)
+    return {"workload": f"batch_sweep_256 ({len(cases)} sessile drops, sides 128-512, seed 4)", "cells": cells,
+            "precision": prec, "value": round(mlups, 2), "unit": "MLUPS", "steps": calls * chunk,
+            "steps_per_call": chunk, "hbm_frac": round(bpl * mlups * 1e6 / 1e9 / hbm_peak, 4), "bytes_per_lu": bpl,
+            "plan": plan, "autotune_s": round(tune_s, 2),
+            "timing": "CUDA events per call; the state is far larger than L2 (no flush)"}
 
 
 def run_batch(args):
@@ -525,7 +692,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sessile_drop_512")
     ap.add_argument("--precision", default="fp64")
-    ap.add_argument("--tile", type=int, nargs=2, default=None)
+    ap.add_argument("--tile", type=int, nargs="+", default=None,
+                    help="bx by [cells per thread]: tile shape of the fused step (2 cells per thread: "
+                         "FP32-arithmetic policies)")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--compare", default="fp16s,df64",
                     help="comma-separated policies timed beside fp64 ('none' to skip)")
@@ -536,6 +705,8 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", default="compound,batch,adjoint",
+                    help="other configurations timed beside the headline ('none' to skip)")
     ap.add_argument("--clocks-dir", default=None, help="directory for the raw nvidia-smi clock samples")
     args = ap.parse_args(argv)
     if args.warmup < 3:

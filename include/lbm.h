@@ -191,6 +191,14 @@ int lbm_debug_bounds(lbm_handle* h, long long* out3);
  * rounding, not bit for bit (each shape is compiled on its own). */
 int lbm_set_tile(lbm_handle* h, int bx, int by);
 
+/* Tile shape and cells per thread of the fused step kernel.  cells_per_thread = 1 is
+ * lbm_set_tile.  cells_per_thread = 2 (policies LBM_FP32, LBM_FP16S, LBM_BF16S) selects the
+ * form in which each thread owns the cells (x, y) and (x, y + 1) and runs their common
+ * arithmetic on packed FP32 pairs: bx x by cells with bx x by / 2 threads, compiled for
+ * 32x8 and 32x16.  Same step, same results to the rounding of contractions.  Other
+ * combinations are LBM_EINVAL. */
+int lbm_set_tile_cells(lbm_handle* h, int bx, int by, int cells_per_thread);
+
 /* Diagnostics sums without any allocation, for callers that cannot allocate device
  * memory when they need them: a host that owns all device memory through its own arena
  * or pool and forbids other allocators, a service whose device memory is fixed when it
@@ -219,6 +227,15 @@ int lbm_set_tile(lbm_handle* h, int bx, int by);
  * library routine is called. */
 int lbm_field_sums_noalloc(const double* phi, const double* fl, int nx, int ny, int N, double* out,
                            void* stream);
+
+/* Measured FP64 instruction rate of the current device, the roofline of the FP64 step
+ * (bound by the FP64 pipe, not by HBM): eight independent chains of FP64 fused
+ * multiply-adds per thread, 8 blocks of 256 threads per SM, timed with CUDA events, the
+ * best of 5 launches after 3 untimed ones.  *ginst_per_s receives FP64 thread-instructions
+ * per second in units of 1e9 (one FMA = 2 flop), *ms (may be NULL) the best launch time.
+ * Allocates and frees a small device buffer; synchronises the device.  A measurement
+ * service of the library (the paper has no counterpart). */
+int lbm_measure_fp64_rate(double* ginst_per_s, double* ms);
 
 /* Message of the last failing call on h.  With h = NULL: the message of the calling
  * thread's last failing call that has no handle (lbm_create, lbm_field_sums_noalloc);
@@ -274,10 +291,10 @@ long long lbm_slab_message_bytes(const lbm_handle* h, int phase);
 int lbm_slab_pack(lbm_handle* h, int side, int phase, void* msg);
 int lbm_slab_unpack(lbm_handle* h, int side, int phase, const void* msg);
 
-/* Diagnostics sums over the band's own rows, into host memory out[2N + 2]: sum phi_p (N),
- * sum (1 - f_l) phi_p (N), max |sum_p phi_p - 1|, and the count of cells where sum_p phi_p,
- * f_l, T, H, u or p is not finite.  Adding the sums (and taking the maximum of the
- * deviation) over all bands gives the lattice's diagnostics.  Synchronises the stream. */
+/* The diagnostics of lbm_get_diagnostics over the band's own rows, into host memory
+ * out[2N + 2]: sum phi_p (N), sum (1 - f_l) phi_p (N), max |sum_p phi_p - 1| and the count of
+ * non-finite cells.  Adding the sums and counts and taking the maximum of the deviation
+ * over all bands gives the lattice's diagnostics.  Synchronises the stream. */
 int lbm_slab_sums(lbm_handle* h, double* out);
 
 /* ---- gradients: the adjoint of the FP64 step -------------------------------------------

@@ -22,25 +22,30 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbo.c")
 _HDR = os.path.join(_HERE, "lbo.h")
 _LIB = os.path.join(_HERE, "liblbo.so")
+_LIB_OMP = os.path.join(_HERE, "liblbo_omp.so")   # the same source built with -fopenmp
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 MAXN = 4
 PERIODIC, WALL, OUTFLOW = 0, 1, 2
 ADIABATIC, DIRICHLET = 0, 1
 
 
-def build(force: bool = False) -> str:
-    """Compile ``lbo.c`` into ``liblbo.so`` (plain gcc, no contraction of a*b+c)."""
-    stale = (not os.path.exists(_LIB)) or any(
-        os.path.getmtime(p) > os.path.getmtime(_LIB) for p in (_SRC, _HDR))
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile ``lbo.c`` into ``liblbo.so`` (plain gcc, no contraction of a*b+c); with
+    omp=True into ``liblbo_omp.so`` with -fopenmp (the per-cell loops run in threads and
+    give bitwise the same results; used only to time the oracle on several cores)."""
+    lib = _LIB_OMP if omp else _LIB
+    stale = (not os.path.exists(lib)) or any(
+        os.path.getmtime(p) > os.path.getmtime(lib) for p in (_SRC, _HDR))
     if force or stale:
-        tmp = _LIB + ".tmp"
-        cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
+        tmp = lib + ".tmp"
+        cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC"] + \
+              (["-fopenmp"] if omp else []) + ["-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.check_call(cmd)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 class Params(ctypes.Structure):
@@ -67,11 +72,11 @@ class Params(ctypes.Structure):
 _DP = ctypes.POINTER(ctypes.c_double)
 
 
-def _load():
-    global _lib
+def _load(omp: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+        if (_lib_omp if omp else _lib) is None:
+            lib = ctypes.CDLL(build(omp=omp))
             lib.lbo_create.restype = ctypes.c_void_p
             lib.lbo_create.argtypes = [ctypes.POINTER(Params), _DP, _DP, _DP, _DP]
             lib.lbo_destroy.argtypes = [ctypes.c_void_p]
@@ -84,8 +89,11 @@ def _load():
             lib.lbo_inverse_map.argtypes = [ctypes.POINTER(Params), _DP, ctypes.c_double]
             lib.lbo_inverse_map.restype = ctypes.c_double
             lib.lbo_stencil.argtypes = [ctypes.POINTER(Params), _DP, _DP, _DP, _DP]
-            _lib = lib
-    return _lib
+            if omp:
+                _lib_omp = lib
+            else:
+                _lib = lib
+    return _lib_omp if omp else _lib
 
 
 def _ptr(a):
@@ -130,8 +138,8 @@ def make_params(case, two_phase_textbook: bool = False, penalty_literal: bool = 
 class Oracle:
     """The CPU oracle on one case: ``step(n)`` then ``fields()``."""
 
-    def __init__(self, case, two_phase_textbook: bool = False, penalty_literal: bool = False):
-        self._lib = _load()
+    def __init__(self, case, two_phase_textbook: bool = False, penalty_literal: bool = False, omp: bool = False):
+        self._lib = _load(omp)
         self.case = case
         self.N, self.nx, self.ny = case.N, case.nx, case.ny
         self._P = make_params(case, two_phase_textbook, penalty_literal)

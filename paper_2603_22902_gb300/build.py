@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
 LIB_CHECK = os.path.join(HERE, "liblbm_gb300_check.so")  # -DLBM_CHECK_BOUNDS debug variant
-UNITS = [f"lbm_kernels_n{n}_{p}.cu" for n in (2, 3, 4) for p in ("fp64", "fp32", "fp16s", "bf16s", "df64")] + ["lbm_capi.cu", "lbm_batch_capi.cu", "lbm_adjoint_capi.cu", "lbm_noalloc.cu", "lbm_slab.cu"]
+UNITS = [f"lbm_kernels_n{n}_{p}.cu" for n in (2, 3, 4) for p in ("fp64", "fp32", "fp16s", "bf16s", "df64")] + ["lbm_capi.cu", "lbm_batch_capi.cu", "lbm_adjoint_capi.cu", "lbm_noalloc.cu", "lbm_slab.cu", "lbm_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -59,12 +59,14 @@ __global__ void init_kernel(const KParams P, const double* __restrict__ phi_in, 
 }
 
 // Diagnostics, pass 1: per-block partial sums (fixed order inside the block) in FP64
-// of sum phi_p, sum f_s phi_p, max |sum_p phi_p - 1| and the count of non-finite cells.
+// of sum phi_p, sum f_s phi_p, max |sum_p phi_p - 1| and the count of non-finite cells,
+// over the cells c0 .. c0 + cells - 1 (the whole lattice, or the own rows of a slab).
 // partial[b * (2N + 2) + k]; pass 2 adds the blocks in index order.
 template <int N, int NT, class Pr>
 __global__ void __launch_bounds__(NT) diag_partial_kernel(const KParams P, const void* __restrict__ pop_base,
                                                           const typename Pr::TA* __restrict__ aux,
-                                                          double* __restrict__ partial)
+                                                          double* __restrict__ partial, long long c0,
+                                                          long long cells)
 {
     constexpr int K = 2 * N + 2;
     __shared__ double red[K][NT];
@@ -73,7 +75,8 @@ __global__ void __launch_bounds__(NT) diag_partial_kernel(const KParams P, const
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    for (long long c = blockIdx.x * (long long)NT + threadIdx.x; c < S; c += (long long)gridDim.x * NT) {
+    for (long long k = blockIdx.x * (long long)NT + threadIdx.x; k < cells; k += (long long)gridDim.x * NT) {
+        const long long c = c0 + k;
         const double den = 1.0 - 0.5 * (double)LBM_LD(P, aux, aux_mdot() * S + c, P.aux_elems, 50);
         double phi[N], sum = 0.0;
 #pragma unroll

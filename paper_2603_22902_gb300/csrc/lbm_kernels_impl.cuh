@@ -8,6 +8,7 @@
 #include "lbm_aux.cuh"
 #include "lbm_batch.cuh"
 #include "lbm_launch.cuh"
+#include "lbm_pair.cuh"
 #include "lbm_step.cuh"
 
 namespace lbm {
@@ -22,6 +23,21 @@ static cudaError_t launch_fused_t(const KParams& P, const void* pin, void* pout,
     return cudaGetLastError();
 }
 
+template <int N, int TX, int TY, bool COLLIDE, class Pr>
+static cudaError_t launch_pair_t(const KParams& P, const void* pin, void* pout, const void* ain, void* aout,
+                                 ExportPtrs ex, cudaStream_t st)
+{
+    using TA = typename Pr::TA;
+    dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+    fused_pair_kernel<N, TX, TY, COLLIDE, Pr><<<grid, TX * TY / 2, 0, st>>>(P, pin, pout, (const TA*)ain, (TA*)aout,
+                                                                            ex);
+    return cudaGetLastError();
+}
+
+// Policies with the two-cells-per-thread form of the step (arithmetic in FP32).
+template <class Pr>
+constexpr bool has_pair_form() { return std::is_same<typename Pr::R, float>::value; }
+
 // The double-word policy is compiled for the 32 x 8 tile only (each shape of its kernel
 // adds much code); lbm_set_tile refuses other shapes for it, and it has no batch form.
 template <class Pr>
@@ -34,6 +50,12 @@ static cudaError_t launch_fused(const KParams& P, const void* pin, void* pout, c
     if constexpr (single_shape<Pr>()) {
         return launch_fused_t<N, 32, 8, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
     } else {
+        if constexpr (has_pair_form<Pr>()) {
+            if (tile == TILE_32x8_PAIR) return launch_pair_t<N, 32, 8, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
+            if (tile == TILE_32x16_PAIR) return launch_pair_t<N, 32, 16, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
+        } else {
+            if (tile >= TILE_32x8_PAIR) return cudaErrorNotSupported;
+        }
         switch (tile) {
             case TILE_32x4: return launch_fused_t<N, 32, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
             case TILE_64x4: return launch_fused_t<N, 64, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
@@ -70,10 +92,12 @@ cudaError_t launch_init(const KParams& P, const double* phi, const double* T, co
 
 template <int N, class Pr>
 cudaError_t launch_diag(const KParams& P, const void* pop, const void* aux, double* partial, double* out,
-                        cudaStream_t st)
+                        cudaStream_t st, long long c0, long long cells)
 {
-    const int nb = diag_blocks(P.S);
-    diag_partial_kernel<N, DIAG_NT, Pr><<<nb, DIAG_NT, 0, st>>>(P, pop, (const typename Pr::TA*)aux, partial);
+    if (cells < 0) cells = P.S - c0;
+    const int nb = diag_blocks(cells);
+    diag_partial_kernel<N, DIAG_NT, Pr><<<nb, DIAG_NT, 0, st>>>(P, pop, (const typename Pr::TA*)aux, partial, c0,
+                                                                cells);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     diag_final_kernel<N><<<1, 32, 0, st>>>(partial, nb, out);
@@ -184,7 +208,8 @@ cudaError_t launch_adj_init(const KParams& P, const double* phi0, const double* 
                                               double*, double*, double*, double*, cudaStream_t);                    \
     template cudaError_t launch_init<N, PR>(const KParams&, const double*, const double*, const double*,           \
                                             const double*, void*, void*, cudaStream_t);                             \
-    template cudaError_t launch_diag<N, PR>(const KParams&, const void*, const void*, double*, double*, cudaStream_t); \
+    template cudaError_t launch_diag<N, PR>(const KParams&, const void*, const void*, double*, double*, cudaStream_t, \
+                                            long long, long long);                                                  \
     template cudaError_t launch_batch_persistent<N, PR>(const BatchTable&, int, int, int, cudaStream_t);            \
     template cudaError_t batch_blocks_per_sm<N, PR>(int, int*);                                                     \
     template cudaError_t launch_batch_step<N, PR>(const BatchTable&, int, int, cudaStream_t);

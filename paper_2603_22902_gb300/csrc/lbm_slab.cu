@@ -73,75 +73,6 @@ __global__ void __launch_bounds__(SLAB_NT) slab_copy_kernel(const SlabRows L, ch
     }
 }
 
-// Sums of the exported fields over rows [r0, r1) of the lattice: per block sum phi_p,
-// sum (1 - f_l) phi_p, max |sum_p phi_p - 1| and the count of cells where sum_p phi_p,
-// f_l, H, u or p is not finite (fixed order inside the block, as the diagnostics).
-template <int N>
-__global__ void __launch_bounds__(SLAB_NT) slab_sums_partial(const double* __restrict__ io, long long S,
-                                                             long long c0, long long cells,
-                                                             double* __restrict__ partial)
-{
-    constexpr int K = 2 * N + 2;
-    __shared__ double red[K][SLAB_NT];
-    double acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    // io planes: phi [N], T, H, fl, ux, uy, p
-    for (long long k = blockIdx.x * (long long)SLAB_NT + threadIdx.x; k < cells; k += (long long)gridDim.x * SLAB_NT) {
-        const long long c = c0 + k;
-        const double fl = io[(N + 2) * S + c];
-        double sum = 0.0;
-#pragma unroll
-        for (int p = 0; p < N; ++p) {
-            const double v = io[p * S + c];
-            acc[p] += v;
-            acc[N + p] += (1.0 - fl) * v;
-            sum += v;
-        }
-        bool bad = !isfinite(sum) || !isfinite(fl);
-#pragma unroll
-        for (int q = N; q < N + 6; ++q) bad = bad || !isfinite(io[q * S + c]);
-        acc[2 * N] = fmax(acc[2 * N], fabs(sum - 1.0));
-        acc[2 * N + 1] += bad ? 1.0 : 0.0;
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) red[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int s = SLAB_NT / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-                red[k][threadIdx.x] = (k == 2 * N) ? fmax(red[k][threadIdx.x], red[k][threadIdx.x + s])
-                                                   : red[k][threadIdx.x] + red[k][threadIdx.x + s];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) partial[blockIdx.x * K + k] = red[k][0];
-}
-
-template <int N>
-__global__ void slab_sums_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out)
-{
-    constexpr int K = 2 * N + 2;
-    const int lane = threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double v = 0.0;
-        for (int b = lane; b < nblocks; b += 32) {
-            const double w = partial[b * K + k];
-            v = (k == 2 * N) ? fmax(v, w) : v + w;
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const double o = __shfl_down_sync(0xffffffffu, v, off);
-            v = (k == 2 * N) ? fmax(v, o) : v + o;
-        }
-        if (lane == 0) out[k] = v;
-    }
-}
-
 int sfail(lbm_handle* h, int code, const std::string& msg)
 {
     if (h) h->err = msg;
@@ -309,37 +240,16 @@ int lbm_slab_sums(lbm_handle* h, double* out)
     if (!h || !out) return sfail(h, LBM_EINVAL, "NULL argument");
     if (!h->slab) return sfail(h, LBM_EINVAL, "not a slab handle");
     if (!h->ready) return sfail(h, LBM_ESTATE, "lbm_set_fields has not been called");
-    cudaError_t e = cudaSetDevice(h->device);
-    const long long S = h->P.S;
     const int N = h->N;
-    double* io = h->io;
-    if (e == cudaSuccess)
-        e = dispatch(N, h->precision, [&](auto n, auto pr) {
-            return launch_export<decltype(n)::value, decltype(pr)>(h->P, h->pop[h->cur], h->aux[h->cur], io,
-                                                                   io + N * S, io + (N + 1) * S, io + (N + 2) * S,
-                                                                   io + (N + 3) * S, io + (N + 4) * S,
-                                                                   io + (N + 5) * S, h->stream);
-        });
+    // the diagnostics of lbm_get_diagnostics over the band's own rows
     const long long c0 = (long long)h->slab_ghost[0] * h->nx;
     const long long cells = (long long)(h->ny - h->slab_ghost[0] - h->slab_ghost[1]) * h->nx;
-    const int nb = diag_blocks(cells);
-    if (e == cudaSuccess) {
-        switch (N) {
-            case 2:
-                slab_sums_partial<2><<<nb, SLAB_NT, 0, h->stream>>>(io, S, c0, cells, h->diag_partial);
-                slab_sums_final<2><<<1, 32, 0, h->stream>>>(h->diag_partial, nb, h->diag_out);
-                break;
-            case 3:
-                slab_sums_partial<3><<<nb, SLAB_NT, 0, h->stream>>>(io, S, c0, cells, h->diag_partial);
-                slab_sums_final<3><<<1, 32, 0, h->stream>>>(h->diag_partial, nb, h->diag_out);
-                break;
-            default:
-                slab_sums_partial<4><<<nb, SLAB_NT, 0, h->stream>>>(io, S, c0, cells, h->diag_partial);
-                slab_sums_final<4><<<1, 32, 0, h->stream>>>(h->diag_partial, nb, h->diag_out);
-                break;
-        }
-        e = cudaGetLastError();
-    }
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess)
+        e = dispatch(N, h->precision, [&](auto n, auto pr) {
+            return launch_diag<decltype(n)::value, decltype(pr)>(h->P, h->pop[h->cur], h->aux[h->cur], h->diag_partial,
+                                                                 h->diag_out, h->stream, c0, cells);
+        });
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, h->diag_out, (2 * N + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

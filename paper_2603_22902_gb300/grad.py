@@ -22,7 +22,13 @@ from . import lbm as L
 
 def theta_gradient(case, g):
     """dL/d(T_wall, Ste, lam_ratio) from the coefficient gradient g (lbm_fl_grad) of a
-    case built with those parameters."""
+    case built with those parameters.
+
+    This is the chain rule of the caller's parameterisation of the loss, not a step of
+    the method: the library differentiates with respect to the coefficients the step
+    uses (wall temperatures, rho_l^p L_p, lambda_s^p, lambda_l^p); how a study maps its own
+    parameters onto them (here L_p = c_p,s (T_m - T_w,ref) / Ste with T_m - T_w,ref = 1, and
+    lambda_s^0 = lam_ratio lambda_l^0) is that study's choice, applied on the host."""
     ste = case.meta["ste"]
     d_ste = 0.0
     for p, ph in enumerate(case.phases):

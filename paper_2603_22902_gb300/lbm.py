@@ -108,6 +108,7 @@ def library():
             lib.lbm_get_steps.argtypes = [_VP]
             lib.lbm_get_steps.restype = ctypes.c_longlong
             lib.lbm_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+            lib.lbm_set_tile_cells.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.lbm_debug_bounds.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong)]
             lib.lbm_debug_bounds.restype = ctypes.c_int
             lib.lbm_last_error.argtypes = [_VP]
@@ -123,6 +124,7 @@ def library():
             lib.lbm_slab_pack.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
             lib.lbm_slab_unpack.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
             lib.lbm_slab_sums.argtypes = [_VP, P(_D)]
+            lib.lbm_measure_fp64_rate.argtypes = [P(_D), P(_D)]
             lib.lbm_batch_create.argtypes = [ctypes.c_int, P(_VP), P(_VP)]
             lib.lbm_batch_set_stream.argtypes = [_VP, _VP]
             lib.lbm_batch_set_plan.argtypes = [_VP, P(lbm_batch_plan)]
@@ -135,8 +137,8 @@ def library():
             lib.lbm_batch_last_error.restype = ctypes.c_char_p
             lib.lbm_batch_destroy.argtypes = [_VP]
             for name in ("lbm_create", "lbm_set_stream", "lbm_set_fields", "lbm_step", "lbm_get_fields",
-                         "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile",
-                         "lbm_slab_create", "lbm_slab_geometry", "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_sums",
+                         "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile", "lbm_set_tile_cells",
+                         "lbm_measure_fp64_rate", "lbm_slab_create", "lbm_slab_geometry", "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_sums",
                          "lbm_batch_create", "lbm_batch_set_stream", "lbm_batch_set_plan", "lbm_batch_get_plan",
                          "lbm_batch_step", "lbm_batch_sync", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_adjoint_fl_loss"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -211,6 +213,13 @@ def lbm_slab_sums(h, N):
     return dict(mass=v[:N], solid=v[N:2 * N], max_sum_dev=v[2 * N], nonfinite=int(v[2 * N + 1]))
 
 
+def lbm_measure_fp64_rate():
+    """(G FP64 thread-instructions per second, best launch ms) of the current device."""
+    r, ms = _D(), _D()
+    _check(library().lbm_measure_fp64_rate(ctypes.byref(r), ctypes.byref(ms)))
+    return r.value, ms.value
+
+
 def lbm_set_stream(h, stream_ptr):
     return _check(library().lbm_set_stream(h, stream_ptr), h)
 
@@ -251,8 +260,8 @@ def lbm_get_steps(h) -> int:
     return int(library().lbm_get_steps(h))
 
 
-def lbm_set_tile(h, bx, by):
-    return _check(library().lbm_set_tile(h, bx, by), h)
+def lbm_set_tile(h, bx, by, cells_per_thread=1):
+    return _check(library().lbm_set_tile_cells(h, bx, by, cells_per_thread), h)
 
 
 def lbm_debug_bounds(h):

@@ -130,14 +130,20 @@ def test_sessile_drop_512_long_parity(lbm, drop_oracle, precision):
         print(precision, n, "steps (error, oracle floor):", fe)
         for k, (err, floor) in fe.items():
             assert err <= max(TOL, 10.0 * floor), (n, k, err, floor)
-    Ob = O[("base", CHECKS[-1])]
-    fs = 1.0 - Ob["fl"]
+    # per-phase volumes: conserved, to 1e-10 relative; solid volumes sum_x f_s phi_p: a
+    # cell of gas below T_m is frozen (f_s = 1) exactly when the liquid's tail there is
+    # positive (a cell without phase-changing material is liquid), so the gas phase's solid
+    # volume moves by whole cells with the sign of tails at the rounding level: within 10x
+    # the oracle's own divergence, like the fields
+    Ob, Op = O[("base", CHECKS[-1])], O[(precision, CHECKS[-1])]
     assert d["nonfinite"] == 0
     for p in range(case.N):
         m = Ob["phi"][p].sum()
         assert abs(d["mass"][p] - m) <= 1e-10 * m
-        sol = (fs * Ob["phi"][p]).sum()
-        assert abs(d["solid"][p] - sol) <= 1e-10 * max(1.0, sol)
+        sol = ((1.0 - Ob["fl"]) * Ob["phi"][p]).sum()
+        floor = abs(((1.0 - Op["fl"]) * Op["phi"][p]).sum() - sol)
+        print(precision, "solid volume", p, d["solid"][p], "oracle", sol, "floor", floor)
+        assert abs(d["solid"][p] - sol) <= max(1e-10 * max(1.0, sol), 10.0 * floor)
 
 
 @pytest.fixture(scope="module")

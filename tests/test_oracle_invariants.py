@@ -230,3 +230,13 @@ def test_uniform_translation_with_equal_densities():
         d = (b - a + n / 2) % n - n / 2
         assert abs(d / (u * steps) - 1.0) < 1e-3, (d, u * steps)
     assert abs(F["ux"].mean() / u0[0] - 1.0) < 1e-3 and abs(F["uy"].mean() / u0[1] - 1.0) < 1e-3
+
+
+def test_openmp_build_is_bitwise_the_serial_oracle():
+    # The benchmark times the oracle also as a -fopenmp build; its per-cell loops write
+    # only their own cells, so the threaded run must give bitwise the same fields.
+    case = W.compound_drop(n=44, R_core=8.0, R_shell=15.0, ny=36, noise=1e-3, mobility=0.02)
+    A = oracle.Oracle(case).step(60).fields()
+    B = oracle.Oracle(case, omp=True).step(60).fields()
+    for k in A:
+        assert np.array_equal(A[k], B[k]), k
