@@ -692,9 +692,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sessile_drop_512")
     ap.add_argument("--precision", default="fp64")
-    ap.add_argument("--tile", type=int, nargs="+", default=None,
-                    help="bx by [cells per thread]: tile shape of the fused step (2 cells per thread: "
-                         "FP32-arithmetic policies)")
+    ap.add_argument("--tile", type=int, nargs=2, default=None)
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--compare", default="fp16s,df64",
                     help="comma-separated policies timed beside fp64 ('none' to skip)")

@@ -191,13 +191,6 @@ int lbm_debug_bounds(lbm_handle* h, long long* out3);
  * rounding, not bit for bit (each shape is compiled on its own). */
 int lbm_set_tile(lbm_handle* h, int bx, int by);
 
-/* Tile shape and cells per thread of the fused step kernel.  cells_per_thread = 1 is
- * lbm_set_tile.  cells_per_thread = 2 (policies LBM_FP32, LBM_FP16S, LBM_BF16S) selects the
- * form in which each thread owns the cells (x, y) and (x, y + 1) and runs their common
- * arithmetic on packed FP32 pairs: bx x by cells with bx x by / 2 threads, compiled for
- * 32x8 and 32x16.  Same step, same results to the rounding of contractions.  Other
- * combinations are LBM_EINVAL. */
-int lbm_set_tile_cells(lbm_handle* h, int bx, int by, int cells_per_thread);
 
 /* Diagnostics sums without any allocation, for callers that cannot allocate device
  * memory when they need them: a host that owns all device memory through its own arena

@@ -226,32 +226,25 @@ int lbm_set_stream(lbm_handle* h, void* stream)
     return LBM_OK;
 }
 
-int lbm_set_tile_cells(lbm_handle* h, int bx, int by, int cells_per_thread)
+int lbm_set_tile(lbm_handle* h, int bx, int by)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
-    if (bx == 0 && by == 0 && cells_per_thread == 1) {
+    if (bx == 0 && by == 0) {
         h->tile = TILE_32x8;
         return LBM_OK;
     }
-    if (cells_per_thread != 1 && cells_per_thread != 2) return fail(h, LBM_EINVAL, "cells_per_thread must be 1 or 2");
-    const bool fp32_math = h->precision == LBM_FP32 || h->precision == LBM_FP16S || h->precision == LBM_BF16S;
-    if (cells_per_thread == 2 && !fp32_math)
-        return fail(h, LBM_EINVAL, "two cells per thread: FP32-arithmetic policies only (LBM_FP32, LBM_FP16S, LBM_BF16S)");
     for (int id = 0; id < TILE_COUNT; ++id) {
         int tx, ty;
         tile_dims(id, tx, ty);
-        if (tx == bx && ty == by && tile_cells_per_thread(id) == cells_per_thread) {
+        if (tx == bx && ty == by) {
             if (h->precision == LBM_DF64 && id != TILE_32x8)
                 return fail(h, LBM_EINVAL, "the LBM_DF64 policy is compiled for the 32x8 tile only");
             h->tile = id;
             return LBM_OK;
         }
     }
-    return fail(h, LBM_EINVAL, cells_per_thread == 1 ? "tile shape not compiled (32x8, 32x4, 64x4, 16x16)"
-                                                     : "tile shape not compiled with two cells per thread (32x8, 32x16)");
+    return fail(h, LBM_EINVAL, "tile shape not compiled (32x8, 32x4, 64x4, 16x16)");
 }
-
-int lbm_set_tile(lbm_handle* h, int bx, int by) { return lbm_set_tile_cells(h, bx, by, 1); }
 
 int lbm_set_fields(lbm_handle* h, const double* phi, const double* T, const double* ux, const double* uy, int where)
 {

@@ -8,7 +8,6 @@
 #include "lbm_aux.cuh"
 #include "lbm_batch.cuh"
 #include "lbm_launch.cuh"
-#include "lbm_pair.cuh"
 #include "lbm_step.cuh"
 
 namespace lbm {
@@ -23,21 +22,6 @@ static cudaError_t launch_fused_t(const KParams& P, const void* pin, void* pout,
     return cudaGetLastError();
 }
 
-template <int N, int TX, int TY, bool COLLIDE, class Pr>
-static cudaError_t launch_pair_t(const KParams& P, const void* pin, void* pout, const void* ain, void* aout,
-                                 ExportPtrs ex, cudaStream_t st)
-{
-    using TA = typename Pr::TA;
-    dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-    fused_pair_kernel<N, TX, TY, COLLIDE, Pr><<<grid, TX * TY / 2, 0, st>>>(P, pin, pout, (const TA*)ain, (TA*)aout,
-                                                                            ex);
-    return cudaGetLastError();
-}
-
-// Policies with the two-cells-per-thread form of the step (arithmetic in FP32).
-template <class Pr>
-constexpr bool has_pair_form() { return std::is_same<typename Pr::R, float>::value; }
-
 // The double-word policy is compiled for the 32 x 8 tile only (each shape of its kernel
 // adds much code); lbm_set_tile refuses other shapes for it, and it has no batch form.
 template <class Pr>
@@ -50,12 +34,6 @@ static cudaError_t launch_fused(const KParams& P, const void* pin, void* pout, c
     if constexpr (single_shape<Pr>()) {
         return launch_fused_t<N, 32, 8, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
     } else {
-        if constexpr (has_pair_form<Pr>()) {
-            if (tile == TILE_32x8_PAIR) return launch_pair_t<N, 32, 8, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
-            if (tile == TILE_32x16_PAIR) return launch_pair_t<N, 32, 16, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
-        } else {
-            if (tile >= TILE_32x8_PAIR) return cudaErrorNotSupported;
-        }
         switch (tile) {
             case TILE_32x4: return launch_fused_t<N, 32, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
             case TILE_64x4: return launch_fused_t<N, 64, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);

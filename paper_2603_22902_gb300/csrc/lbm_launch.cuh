@@ -11,24 +11,18 @@
 
 namespace lbm {
 
-// Compiled tile shapes of the fused step kernel: TX x TY threads, one cell each, and
-// (the FP32-arithmetic policies) TX x TY cells with two cells per thread, TX x TY/2 threads.
-enum TileId {
-    TILE_32x8 = 0, TILE_32x4 = 1, TILE_64x4 = 2, TILE_16x16 = 3,
-    TILE_32x8_PAIR = 4, TILE_32x16_PAIR = 5, TILE_COUNT = 6
-};
+// Compiled tile shapes of the fused step kernel (TX x TY threads, one cell each).
+enum TileId { TILE_32x8 = 0, TILE_32x4 = 1, TILE_64x4 = 2, TILE_16x16 = 3, TILE_COUNT = 4 };
 inline bool tile_dims(int id, int& tx, int& ty)
 {
     switch (id) {
-        case TILE_32x8: case TILE_32x8_PAIR: tx = 32; ty = 8; return true;
+        case TILE_32x8: tx = 32; ty = 8; return true;
         case TILE_32x4: tx = 32; ty = 4; return true;
         case TILE_64x4: tx = 64; ty = 4; return true;
         case TILE_16x16: tx = 16; ty = 16; return true;
-        case TILE_32x16_PAIR: tx = 32; ty = 16; return true;
         default: return false;
     }
 }
-inline int tile_cells_per_thread(int id) { return id >= TILE_32x8_PAIR ? 2 : 1; }
 
 template <int N, class Pr>
 cudaError_t launch_step(const KParams& P, const void* pin, void* pout, const void* ain, void* aout, int tile,

@@ -108,7 +108,6 @@ def library():
             lib.lbm_get_steps.argtypes = [_VP]
             lib.lbm_get_steps.restype = ctypes.c_longlong
             lib.lbm_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
-            lib.lbm_set_tile_cells.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.lbm_debug_bounds.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong)]
             lib.lbm_debug_bounds.restype = ctypes.c_int
             lib.lbm_last_error.argtypes = [_VP]
@@ -137,7 +136,7 @@ def library():
             lib.lbm_batch_last_error.restype = ctypes.c_char_p
             lib.lbm_batch_destroy.argtypes = [_VP]
             for name in ("lbm_create", "lbm_set_stream", "lbm_set_fields", "lbm_step", "lbm_get_fields",
-                         "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile", "lbm_set_tile_cells",
+                         "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile",
                          "lbm_measure_fp64_rate", "lbm_slab_create", "lbm_slab_geometry", "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_sums",
                          "lbm_batch_create", "lbm_batch_set_stream", "lbm_batch_set_plan", "lbm_batch_get_plan",
                          "lbm_batch_step", "lbm_batch_sync", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_adjoint_fl_loss"):
@@ -260,8 +259,8 @@ def lbm_get_steps(h) -> int:
     return int(library().lbm_get_steps(h))
 
 
-def lbm_set_tile(h, bx, by, cells_per_thread=1):
-    return _check(library().lbm_set_tile_cells(h, bx, by, cells_per_thread), h)
+def lbm_set_tile(h, bx, by):
+    return _check(library().lbm_set_tile(h, bx, by), h)
 
 
 def lbm_debug_bounds(h):
