@@ -63,16 +63,16 @@ ISSUE_PEAK_GWINST = 152 * 4 * 2.070
 # from the kernel sources with digest `digest` (build.kernel_digest; sessile drop 512^2,
 # N = 2, 32 x 8 tiles):
 # FP64-pipe thread-instructions, FP64 flop (DFMA = 2, DADD / DMUL = 1), warp-instructions
-# issued, FP32 thread-instructions (FADD + FADD2 + FMUL + FFMA; a packed FADD2 counts
-# once) and DRAM bytes.
+# issued, FP32 thread-instructions (FADD + FMUL + FFMA; the packed FADD2 of the double-word
+# sums is not among them) and DRAM bytes.
 # A changed kernel has another digest, and then these counts are not reported.
 # (DRAM bytes are what ncu saw during the launch: part of the writes of a launch is
 # still in L2 when it ends and reaches DRAM during the next one.)
-_D = "8f01deb8d5a02cfad9316cdb380318ef8e74c12e414c69fbceca33ef64bcb0c4"
+_D = "d38540d008cb7d235e911051458fc37dbb6b5db0c23210af5acc86e62315394e"
 NCU_COUNTS = {
-    ("fp64", 2): {"digest": _D, "fp64_inst": 487.0, "fp64_flop": 660.9, "warp_inst": 102.4, "dram_bytes": 518.7},
-    ("df64", 2): {"digest": _D, "fp64_inst": 0.08, "warp_inst": 176.0, "fp32_inst": 4406.3, "dram_bytes": 645.9},
-    ("fp16s", 2): {"digest": _D, "fp64_inst": 0.06, "fp64_flop": 0.02, "warp_inst": 50.8, "dram_bytes": 108.4},
+    ("fp64", 2): {"digest": _D, "fp64_inst": 487.0, "fp64_flop": 660.8, "warp_inst": 102.4, "dram_bytes": 518.7},
+    ("df64", 2): {"digest": _D, "fp64_inst": 0.08, "warp_inst": 176.0, "fp32_inst": 4089.1, "dram_bytes": 648.6},
+    ("fp16s", 2): {"digest": _D, "fp64_inst": 0.06, "fp64_flop": 0.04, "warp_inst": 50.8, "dram_bytes": 108.5},
 }
 
 
@@ -217,6 +217,15 @@ def host_info():
     except OSError:
         pass
     if not model:
+        try:  # Arm hosts: /proc/cpuinfo has no model name, lscpu maps the part number
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    if not model:
         import platform
         model = platform.processor() or platform.machine()
     try:
@@ -334,6 +343,8 @@ def run_gpu(args):
                 "frac": round(gbs / hbm_peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} (copy bandwidth)", "bytes_per_lu": bpl, "lu_per_launch": cells}
     roofline = roof_hbm
+    if args.precision == "fp64":
+        roof_hbm["fp64_rate"] = {"peak": round(fp64_peak, 1), "unit": "G FP64-pipe inst/s", "peak_kind": fp64_peak_kind}
     if counts and args.precision == "fp64":
         gi = counts["fp64_inst"] * mlups_rank * 1e6 / 1e9
         roofline = {"bound": "alu", "achieved": round(gi, 1), "peak": round(fp64_peak, 1),

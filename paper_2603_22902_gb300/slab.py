@@ -87,9 +87,12 @@ class LocalExchange:
 
 
 class DistExchange:
-    """One band per rank of a torch.distributed group (rank k holds band k)."""
+    """One band per rank of a torch.distributed group (rank k holds band k).  `alloc`
+    gives the message buffers that pack and unpack use; with `host_alloc` (a backend that
+    moves host memory only, e.g. gloo) the messages travel through host buffers of that
+    size, copied to and from the message buffers on the current stream."""
 
-    def __init__(self, band, periodic, alloc, dist=None):
+    def __init__(self, band, periodic, alloc, dist=None, host_alloc=None):
         if dist is None:
             import torch.distributed as dist
         self.dist = dist
@@ -98,22 +101,33 @@ class DistExchange:
         self.below, self.above = neighbours(self.rank, n, periodic)
         self.send = {(side, ph): alloc(band.msg_bytes[ph]) for side in (YMIN, YMAX) for ph in (1, 2)}
         self.recv = {(side, ph): alloc(band.msg_bytes[ph]) for side in (YMIN, YMAX) for ph in (1, 2)}
+        self.host_send = self.host_recv = None
+        if host_alloc is not None:
+            self.host_send = {k: host_alloc(band.msg_bytes[k[1]]) for k in self.send}
+            self.host_recv = {k: host_alloc(band.msg_bytes[k[1]]) for k in self.recv}
 
     def _transfer(self, ph):
         """Round 1: y-max messages go up (received on the y-min side); round 2: y-min
         messages go down (received on the y-max side).  Each round is one batch of
         point-to-point operations, posted in the same order on every rank."""
         d = self.dist
+        staged = self.host_send is not None
+        sbuf = self.host_send if staged else self.send
+        rbuf = self.host_recv if staged else self.recv
         for send_side, peer_send, recv_side, peer_recv in ((YMAX, self.above, YMIN, self.below),
                                                           (YMIN, self.below, YMAX, self.above)):
             ops = []
             if peer_send is not None:
-                ops.append(d.P2POp(d.isend, self.send[(send_side, ph)], peer_send, tag=10 * ph + send_side))
+                if staged:
+                    sbuf[(send_side, ph)].copy_(self.send[(send_side, ph)])
+                ops.append(d.P2POp(d.isend, sbuf[(send_side, ph)], peer_send, tag=10 * ph + send_side))
             if peer_recv is not None:
-                ops.append(d.P2POp(d.irecv, self.recv[(recv_side, ph)], peer_recv, tag=10 * ph + (5 - recv_side)))
+                ops.append(d.P2POp(d.irecv, rbuf[(recv_side, ph)], peer_recv, tag=10 * ph + (5 - recv_side)))
             if ops:
                 for req in d.batch_isend_irecv(ops):
                     req.wait()
+            if staged and peer_recv is not None:
+                self.recv[(recv_side, ph)].copy_(rbuf[(recv_side, ph)])
 
     def exchange(self):
         b = self.band

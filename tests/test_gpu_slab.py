@@ -4,8 +4,13 @@ step, must step exactly like the single handle on the whole lattice.  Every cell
 computed by the same kernel from the same inputs, so the bands' own rows must equal the
 single run to 1e-12 (bit for bit in practice), on walls, outflow and periodic y sides,
 N = 2, 3, 4, FP64, double words and FP16 storage; the bands' diagnostics sums, combined,
-must equal the single handle's diagnostics; and one run is checked against the CPU
-oracle to the parity bar."""
+must equal the single handle's diagnostics; one run is checked against the CPU oracle
+to the parity bar; and two processes, one band each on the same GPU, exchanging their
+messages through torch.distributed (gloo, host buffers) as ranks of a multi-GPU run do
+(NCCL, device buffers), step exactly like the single handle too."""
+import os
+import socket
+
 import numpy as np
 import pytest
 
@@ -119,3 +124,59 @@ def test_slab_arguments(lbm):
         s.pack(3, 3, msg)                       # phases are 1 and 2
     assert e.value.code == L.LBM_EINVAL
     s.close()
+
+
+def _rank_worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch
+    import torch.distributed as dist
+    from paper_2603_22902_gb300 import lbm as L
+    from paper_2603_22902_gb300.slab import DistExchange
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    case = W.compound_drop(n=48, R_core=8.0, R_shell=15.0, ny=40, noise=1e-3, mobility=0.02)
+    y0, y1 = split_rows(case.ny, world)[rank]
+    band = L.SlabSolver(case, y0, y1).set_fields()
+    ex = DistExchange(band, case.bc[2] == W.PERIODIC,
+                      alloc=lambda n: torch.empty(n, dtype=torch.uint8, device="cuda"),
+                      host_alloc=lambda n: torch.empty(n, dtype=torch.uint8))
+    ex.step(150)
+    F = band.own(band.fields_numpy())
+    sums = ex.sums(case.N)
+    band.close()
+    dist.destroy_process_group()
+    q.put((rank, F, sums))
+
+
+def test_bands_on_two_ranks_equal_the_single_lattice(lbm):
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = {}
+    for _ in procs:
+        r, F, sums = q.get(timeout=300)
+        out[r] = (F, sums)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    case = W.compound_drop(n=48, R_core=8.0, R_shell=15.0, ny=40, noise=1e-3, mobility=0.02)
+    s = lbm.Solver(case).set_fields()
+    s.step(150)
+    R = s.fields_numpy()
+    d = s.diagnostics()
+    s.close()
+    F = {k: np.concatenate([out[0][0][k], out[1][0][k]], axis=-2) for k in FIELDS}
+    errs = {k: float(np.abs(F[k] - R[k]).max()) for k in FIELDS}
+    print("two ranks", errs)
+    assert all(v <= 1e-12 for v in errs.values()), errs
+    for r in (0, 1):
+        sums = out[r][1]
+        for p in range(case.N):
+            assert abs(sums["mass"][p] - d["mass"][p]) <= 1e-12 * max(1.0, d["mass"][p])
+        assert sums["nonfinite"] == 0
