@@ -192,6 +192,18 @@ int lbm_debug_bounds(lbm_handle* h, long long* out3);
 int lbm_set_tile(lbm_handle* h, int bx, int by);
 
 
+/* Step with its inputs staged in shared memory by the tensor-memory accelerator: a
+ * persistent grid of two blocks per SM, each copying the next interior 32x8 tile's
+ * populations and lagged values (tile and ring) into one half of a double buffer while it
+ * computes the current tile from the other (the arithmetic is that of lbm_step, cell by
+ * cell); tiles that touch a side of the lattice are stepped from global memory.  A
+ * service of the library for LBM_FP16S and LBM_BF16S handles with N = 2, nx a multiple of 8
+ * and the 32x8 tile; LBM_EINVAL otherwise, LBM_ECUDA when the tensor maps cannot be
+ * encoded.  on = 0 returns to the one-launch-per-step form.  Every wait for a copy is
+ * bounded; a wait that gave up is reported as LBM_ETIMEOUT by the next lbm_step with
+ * diag_every > 0 or lbm_get_diagnostics, with the state undefined. */
+int lbm_set_staging(lbm_handle* h, int on);
+
 /* Diagnostics sums without any allocation, for callers that cannot allocate device
  * memory when they need them: a host that owns all device memory through its own arena
  * or pool and forbids other allocators, a service whose device memory is fixed when it

@@ -1,5 +1,7 @@
 // lbm_capi.cu -- the C ABI declared in include/lbm.h: handle, parameter checks and
 // derivations (Sections 2-3 of arXiv 2603.22902), device memory, launches.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -11,6 +13,7 @@
 #include "../../include/lbm.h"
 #include "lbm_handle.hpp"
 #include "lbm_launch.cuh"
+#include "lbm_staged.cuh"
 
 using namespace lbm;
 
@@ -52,6 +55,8 @@ static void free_all(lbm_handle* h)
     cudaFree(h->diag_partial);
     cudaFree(h->diag_out);
     cudaFree(h->dbg);
+    cudaFree(h->stage_status);
+    h->stage_status = nullptr;
     h->io = h->diag_partial = h->diag_out = nullptr;
     h->dbg = nullptr;
 }
@@ -76,6 +81,59 @@ static Coef<float> round_coef(const Coef<double>& d)
     float* dst = reinterpret_cast<float*>(&f);
     for (size_t k = 0; k < sizeof(Coef<double>) / sizeof(double); ++k) dst[k] = (float)src[k];
     return f;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver
+// library); NULL when the driver does not provide it.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// One 3D tensor map over `planes` planes [ny][nx] of esz-byte elements at base, with box
+// (bx, by, bz).
+static bool encode_map(CUtensorMap* m, void* base, int esz, int nx, int ny, int planes, int bx, int by, int bz)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const CUtensorMapDataType dt = esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                   : esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32
+                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * esz, (cuuint64_t)nx * ny * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The six maps of population set k and lagged set k (boxes A..F of lbm_staged.cuh).
+template <int N, class Pr>
+static bool encode_stage_maps(lbm_handle* h, int k, StageMaps& M)
+{
+    using Lay = StageLayout<N, Pr>;
+    const int nx = h->nx, ny = h->ny;
+    char* rest = (char*)h->pop[k];
+    char* move = rest + h->P.rest_elems * Lay::ER;
+    char* aux = (char*)h->aux[k];
+    return encode_map(&M.m[0], move, Lay::EM, nx, ny, 8 * (N + 2), STAGE_TX, STAGE_TY, 8) &&
+           encode_map(&M.m[1], move, Lay::EM, nx, ny, 8 * (N + 2), Lay::WM, Lay::H, 8 * (N + 1)) &&
+           encode_map(&M.m[2], rest, Lay::ER, nx, ny, N + 2, STAGE_TX, STAGE_TY, 1) &&
+           encode_map(&M.m[3], rest, Lay::ER, nx, ny, N + 2, Lay::WR, Lay::H, N + 1) &&
+           encode_map(&M.m[4], aux, Lay::EA, nx, ny, 3 + 2 * N, Lay::WA, Lay::H, 2) &&
+           encode_map(&M.m[5], aux, Lay::EA, nx, ny, 3 + 2 * N, STAGE_TX, STAGE_TY, 1 + 2 * N);
 }
 
 extern "C" {
@@ -239,11 +297,38 @@ int lbm_set_tile(lbm_handle* h, int bx, int by)
         if (tx == bx && ty == by) {
             if (h->precision == LBM_DF64 && id != TILE_32x8)
                 return fail(h, LBM_EINVAL, "the LBM_DF64 policy is compiled for the 32x8 tile only");
+            if (h->staged && id != TILE_32x8) return fail(h, LBM_EINVAL, "the staged step uses the 32x8 tile");
             h->tile = id;
             return LBM_OK;
         }
     }
     return fail(h, LBM_EINVAL, "tile shape not compiled (32x8, 32x4, 64x4, 16x16)");
+}
+
+int lbm_set_staging(lbm_handle* h, int on)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!on) {
+        h->staged = false;
+        return LBM_OK;
+    }
+    if ((h->precision != LBM_FP16S && h->precision != LBM_BF16S) || h->N != 2)
+        return fail(h, LBM_EINVAL, "the staged step is compiled for LBM_FP16S and LBM_BF16S with N = 2");
+    if (h->nx % 8 != 0) return fail(h, LBM_EINVAL, "the staged step needs nx a multiple of 8 (16-byte rows)");
+    if (h->tile != TILE_32x8) return fail(h, LBM_EINVAL, "the staged step uses the 32x8 tile");
+    LBM_CUDA_TRY(h, cudaSetDevice(h->device));
+    if (!h->sms) LBM_CUDA_TRY(h, cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
+    if (!h->stage_status) {
+        LBM_CUDA_TRY(h, cudaMalloc(&h->stage_status, sizeof(int)));
+        LBM_CUDA_TRY(h, cudaMemset(h->stage_status, 0, sizeof(int)));
+    }
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k)
+        ok = h->precision == LBM_FP16S ? encode_stage_maps<2, PrecFP16S>(h, k, h->stage_maps[k])
+                                       : encode_stage_maps<2, PrecBF16S>(h, k, h->stage_maps[k]);
+    if (!ok) return fail(h, LBM_ECUDA, "tensor maps of the staged step could not be encoded");
+    h->staged = true;
+    return LBM_OK;
 }
 
 int lbm_set_fields(lbm_handle* h, const double* phi, const double* T, const double* ux, const double* uy, int where)
@@ -280,6 +365,20 @@ int lbm_set_fields(lbm_handle* h, const double* phi, const double* T, const doub
     return LBM_OK;
 }
 
+// LBM_ETIMEOUT (and the status word cleared) when a staged step gave up an mbarrier wait.
+static int check_stage_status(lbm_handle* h)
+{
+    if (!h->stage_status) return LBM_OK;
+    int st = 0;
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(&st, h->stage_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (st != 0) {
+        LBM_CUDA_TRY(h, cudaMemsetAsync(h->stage_status, 0, sizeof(int), h->stream));
+        return fail(h, LBM_ETIMEOUT, "a staged step gave up waiting for its tensor copies; the state is undefined");
+    }
+    return LBM_OK;
+}
+
 static int run_diag(lbm_handle* h, double* host_out)
 {
     cudaError_t e = dispatch(h->N, h->precision, [&](auto n, auto pr) {
@@ -290,7 +389,7 @@ static int run_diag(lbm_handle* h, double* host_out)
     LBM_CUDA_TRY(h, cudaMemcpyAsync(host_out, h->diag_out, (2 * h->N + 2) * sizeof(double), cudaMemcpyDeviceToHost,
                                     h->stream));
     LBM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    return LBM_OK;
+    return check_stage_status(h);
 }
 
 int lbm_step(lbm_handle* h, long nsteps)
@@ -302,6 +401,10 @@ int lbm_step(lbm_handle* h, long nsteps)
     for (long n = 0; n < nsteps; ++n) {
         const int a = h->cur, b = a ^ 1;
         cudaError_t e = dispatch(h->N, h->precision, [&](auto n, auto pr) {
+            if (h->staged)
+                return launch_staged<decltype(n)::value, decltype(pr)>(h->P, h->stage_maps[a], h->pop[a], h->pop[b],
+                                                                       h->aux[a], h->aux[b], h->stage_status, h->sms,
+                                                                       h->stream);
             return launch_step<decltype(n)::value, decltype(pr)>(h->P, h->pop[a], h->pop[b], h->aux[a], h->aux[b],
                                                                  h->tile, h->stream);
         });

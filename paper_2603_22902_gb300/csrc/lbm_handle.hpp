@@ -27,6 +27,11 @@ struct lbm_handle {
     bool ready = false;
     long long steps = 0;
     cudaStream_t stream = nullptr;
+    // TMA-staged step (lbm_set_staging): tensor maps of both population sets, status word
+    bool staged = false;
+    lbm::StageMaps stage_maps[2];
+    int* stage_status = nullptr;
+    int sms = 0;
     // y slab (lbm_slab_create): ghost rows below / above the band, first global row
     bool slab = false;
     int slab_ghost[2] = {0, 0};

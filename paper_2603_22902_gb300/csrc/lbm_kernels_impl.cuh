@@ -8,6 +8,7 @@
 #include "lbm_aux.cuh"
 #include "lbm_batch.cuh"
 #include "lbm_launch.cuh"
+#include "lbm_staged.cuh"
 #include "lbm_step.cuh"
 
 namespace lbm {
@@ -56,6 +57,27 @@ cudaError_t launch_export(const KParams& P, const void* pin, const void* ain, do
 {
     return launch_fused<N, false, Pr>(P, pin, nullptr, ain, nullptr, ExportPtrs{phi, T, H, fl, ux, uy, p}, TILE_32x8,
                                       st);
+}
+
+template <int N, class Pr>
+cudaError_t launch_staged(const KParams& P, const StageMaps& maps, const void* pin, void* pout, const void* ain,
+                          void* aout, int* status, int sms, cudaStream_t st)
+{
+    if constexpr (staged_policy<Pr>() && N == 2) {
+        using Lay = StageLayout<N, Pr>;
+        using TA = typename Pr::TA;
+        cudaError_t e = cudaFuncSetAttribute(staged_step_kernel<N, Pr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Lay::TOTAL);
+        if (e != cudaSuccess) return e;
+        const int tiles_x = (P.nx + STAGE_TX - 1) / STAGE_TX, tiles_y = (P.ny + STAGE_TY - 1) / STAGE_TY;
+        const int ntiles = tiles_x * tiles_y;
+        const int grid = std::min(ntiles, 2 * sms);
+        staged_step_kernel<N, Pr><<<grid, STAGE_NT, Lay::TOTAL, st>>>(P, maps, pin, pout, (const TA*)ain, (TA*)aout,
+                                                                      tiles_x, ntiles, status);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
 }
 
 template <int N, class Pr>
@@ -182,6 +204,8 @@ cudaError_t launch_adj_init(const KParams& P, const double* phi0, const double* 
 #define LBM_INSTANTIATE(N, PR)                                                                                      \
     template cudaError_t launch_step<N, PR>(const KParams&, const void*, void*, const void*, void*, int,           \
                                             cudaStream_t);                                                          \
+    template cudaError_t launch_staged<N, PR>(const KParams&, const StageMaps&, const void*, void*, const void*,   \
+                                              void*, int*, int, cudaStream_t);                                      \
     template cudaError_t launch_export<N, PR>(const KParams&, const void*, const void*, double*, double*, double*, \
                                               double*, double*, double*, double*, cudaStream_t);                    \
     template cudaError_t launch_init<N, PR>(const KParams&, const double*, const double*, const double*,           \

@@ -2,6 +2,7 @@
 // instantiation set per phase count N and precision policy (lbm_kernels_*.cu).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -33,6 +34,20 @@ cudaError_t launch_export(const KParams& P, const void* pin, const void* ain, do
 template <int N, class Pr>
 cudaError_t launch_init(const KParams& P, const double* phi, const double* T, const double* ux, const double* uy,
                         void* pop, void* aux, cudaStream_t st);
+// The step with its inputs staged by the TMA (lbm_staged.cuh): policies with 16-bit moving
+// populations, N = 2.  maps are the six tensor maps of the input set; status receives 1
+// when an mbarrier wait gave up.  cudaErrorNotSupported for other policies.
+struct StageMaps {
+    CUtensorMap m[6];   // boxes A..F of lbm_staged.cuh
+};
+template <int N, class Pr>
+cudaError_t launch_staged(const KParams& P, const StageMaps& maps, const void* pin, void* pout, const void* ain,
+                          void* aout, int* status, int sms, cudaStream_t st);
+template <class Pr>
+constexpr bool staged_policy()
+{
+    return Pr::QUANT;
+}
 // Two-pass deterministic reduction; partial must hold diag_blocks() * (2N + 2) doubles,
 // out 2N + 2 doubles (mass[N], solid[N], max |sum phi - 1|, non-finite count).
 constexpr int DIAG_NT = 256;

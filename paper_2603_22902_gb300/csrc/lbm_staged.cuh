@@ -1,0 +1,223 @@
+// lbm_staged.cuh -- the fused step with its inputs staged in shared memory by the
+// tensor-memory accelerator (TMA), for the 16-bit storage policies.
+//
+// The one-cell step (lbm_step.cuh) is bound by the latency of its global loads: every
+// block loads its tile's and ring's populations, waits, computes, loads the flow
+// populations, waits again.  Here a persistent grid of two blocks per SM walks the tiles
+// of the lattice; while a block computes one interior 32 x 8 tile from shared memory, the
+// TMA copies the next tile's inputs into the other half of a double buffer, so the copy
+// of tile k + 1 overlaps the arithmetic of tile k.  Six tensor copies per tile, issued by
+// one thread and completing on one mbarrier:
+//   A  the eight moving planes of f, own cells          [8][8][32]
+//   B  the moving planes of g_p and h, tile and ring     [8(N+1)][10][32 + 2 pad]
+//   C  the rest plane of f, own cells                    [1][8][32]
+//   D  the rest planes of g_p and h, tile and ring        [N+1][10][32 + 2 pad]
+//   E  the lagged mdot' and Q', tile and ring             [2][10][32 + 2 pad]
+//   F  the other lagged planes, own cells                 [1 + 2N][8][32]
+// A box that includes the ring starts pad = 16 / element-size cells left of the tile, so
+// its first x coordinate is on a 16-byte boundary (the tile's x0 is a multiple of 32),
+// and is 16-byte multiples wide; its rows y0 - 1 .. y0 + 8 lie inside the lattice for an
+// interior tile, and columns beyond the right side are filled with zeros and never read.
+// The arithmetic is step_tile_l of the one-cell step with a loader that reads the staged
+// copy, so every interior cell is computed exactly as the one-cell step computes it; tiles
+// that touch a side of the lattice run the one-cell step itself from global memory.
+// Every wait on an mbarrier is bounded: a wait that gives up sets a status word (reported
+// as LBM_ETIMEOUT), waits (bounded) for the block's own copies in flight and leaves.
+#pragma once
+
+#include "lbm_launch.cuh"
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+constexpr int STAGE_TX = 32, STAGE_TY = 8, STAGE_NT = STAGE_TX * STAGE_TY;
+constexpr long long STAGE_WAIT_LIMIT = 1LL << 22;   // try_wait polls of one mbarrier wait
+
+__host__ __device__ constexpr int stage_round(int b) { return (b + 127) / 128 * 128; }
+
+// Layout of one staged tile in shared memory (bytes; every box on a 128-byte boundary).
+template <int N, class Pr>
+struct StageLayout {
+    static constexpr int EM = sizeof(typename Pr::TM), ER = sizeof(typename Pr::TR), EA = sizeof(typename Pr::TA);
+    static constexpr int PM = 16 / EM, PR = 16 / ER, PA = 16 / EA;          // pads (cells)
+    static constexpr int WM = STAGE_TX + 2 * PM, WR = STAGE_TX + 2 * PR, WA = STAGE_TX + 2 * PA;
+    static constexpr int H = STAGE_TY + 2;
+    static constexpr int A = 8 * STAGE_TY * STAGE_TX * EM;
+    static constexpr int B = 8 * (N + 1) * H * WM * EM;
+    static constexpr int C = STAGE_TY * STAGE_TX * ER;
+    static constexpr int D = (N + 1) * H * WR * ER;
+    static constexpr int E = 2 * H * WA * EA;
+    static constexpr int F = (1 + 2 * N) * STAGE_TY * STAGE_TX * EA;
+    static constexpr int OA = 0, OB = OA + stage_round(A), OC = OB + stage_round(B), OD = OC + stage_round(C),
+                         OE = OD + stage_round(D), OF = OE + stage_round(E), BYTES = OF + stage_round(F);
+    static constexpr int TX_BYTES = A + B + C + D + E + F;   // what the six copies deliver
+    // dynamic shared memory of a block: two stages, two mbarriers, the one-cell step's tile
+    static constexpr int SMEM_ONE = tile_smem_elems<N, STAGE_TX, STAGE_TY, Pr>() * (int)sizeof(typename Pr::R);
+    // (TOTAL has 128 bytes of slack: the kernel aligns its base to 128 bytes)
+    static constexpr int OBAR = 2 * BYTES, OONE = OBAR + 128, TOTAL = OONE + stage_round(SMEM_ONE) + 128;
+};
+
+// Reads of one staged interior tile; a cell is (lx, ly) of the tile with its ring.
+template <int N, class Pr>
+struct StagedLoader {
+    using R = typename Pr::R;
+    using TR = typename Pr::TR;
+    using TM = typename Pr::TM;
+    using TA = typename Pr::TA;
+    using Lay = StageLayout<N, Pr>;
+    using Cell = int;   // ly * 64 + lx
+    const KParams& P;
+    const unsigned char* st;   // the stage
+    __device__ __forceinline__ bool locate(int lx, int ly, Cell& cell) const
+    {
+        cell = ly * 64 + lx;
+        return true;
+    }
+    __device__ __forceinline__ Cell own(int, int, int tx, int ty) const { return (ty + 1) * 64 + tx + 1; }
+    template <int KIND>
+    __device__ __forceinline__ R pop(int s, int i, Cell c, int) const
+    {
+        const int lx = c & 63, ly = c >> 6;
+        if (s == 0) {  // the flow populations: own cells only
+            const int o = (ly - 1) * STAGE_TX + (lx - 1);
+            if (i == 0) return (R) reinterpret_cast<const TR*>(st + Lay::OC)[o];
+            return dequant<Pr, KIND>(P, reinterpret_cast<const TM*>(st + Lay::OA)[(i - 1) * STAGE_TY * STAGE_TX + o], i);
+        }
+        if (i == 0) return (R) reinterpret_cast<const TR*>(st + Lay::OD)[((s - 1) * Lay::H + ly) * Lay::WR + lx - 1 + Lay::PR];
+        const int plane = (s - 1) * 8 + i - 1;
+        return dequant<Pr, KIND>(P, reinterpret_cast<const TM*>(st + Lay::OB)[(plane * Lay::H + ly) * Lay::WM + lx - 1 + Lay::PM],
+                                 i);
+    }
+    template <int KIND>
+    __device__ __forceinline__ R pop_late(int s, int i, Cell c, int site) const
+    {
+        return pop<KIND>(s, i, c, site);
+    }
+    __device__ __forceinline__ R aux(int a, Cell c, int) const
+    {
+        const int lx = c & 63, ly = c >> 6;
+        if (a < 2) return (R) reinterpret_cast<const TA*>(st + Lay::OE)[(a * Lay::H + ly) * Lay::WA + lx - 1 + Lay::PA];
+        return (R) reinterpret_cast<const TA*>(st + Lay::OF)[((a - 2) * STAGE_TY + ly - 1) * STAGE_TX + lx - 1];
+    }
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait for the phase `parity` of an mbarrier to complete.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+{
+    for (long long k = 0; k < STAGE_WAIT_LIMIT; ++k)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+// An interior tile for staging: its ring lies inside the lattice (no wrap, no boundary
+// rule), and its x0 leaves room for the left pad of the boxes.
+__device__ __forceinline__ bool stage_interior(const KParams& P, int bx, int by)
+{
+    const int x0 = bx * STAGE_TX, y0 = by * STAGE_TY;
+    return x0 >= STAGE_TX && x0 + STAGE_TX <= P.nx - 1 && y0 >= 1 && y0 + STAGE_TY <= P.ny - 1;
+}
+
+// Thread 0: the six copies of tile (bx, by) into `stage`, completing on `bar`.
+template <int N, class Pr>
+__device__ __forceinline__ void stage_issue(const StageMaps& M, unsigned char* stage, unsigned bar, int bx, int by)
+{
+    using Lay = StageLayout<N, Pr>;
+    const int x0 = bx * STAGE_TX, y0 = by * STAGE_TY;
+    // the previous readers of this stage (generic proxy) are ordered before the copies
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect(bar, (unsigned)Lay::TX_BYTES);
+    const unsigned s = smem_addr(stage);
+    tma_load_3d(s + Lay::OA, &M.m[0], x0, y0, 0, bar);
+    tma_load_3d(s + Lay::OB, &M.m[1], x0 - Lay::PM, y0 - 1, 8, bar);
+    tma_load_3d(s + Lay::OC, &M.m[2], x0, y0, 0, bar);
+    tma_load_3d(s + Lay::OD, &M.m[3], x0 - Lay::PR, y0 - 1, 1, bar);
+    tma_load_3d(s + Lay::OE, &M.m[4], x0 - Lay::PA, y0 - 1, 0, bar);
+    tma_load_3d(s + Lay::OF, &M.m[5], x0, y0, 2, bar);
+}
+
+// One step over all tiles of the lattice: a persistent grid, tiles in order t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; interior tiles from a double-buffered staged copy, the
+// others by the one-cell step.
+template <int N, class Pr>
+__global__ void __launch_bounds__(STAGE_NT, 2)
+staged_step_kernel(const KParams P, const __grid_constant__ StageMaps M, const void* __restrict__ pin_base,
+                   void* __restrict__ pout_base, const typename Pr::TA* __restrict__ ain,
+                   typename Pr::TA* __restrict__ aout, int tiles_x, int ntiles, int* __restrict__ status)
+{
+    using Lay = StageLayout<N, Pr>;
+    using R = typename Pr::R;
+    extern __shared__ __align__(128) unsigned char dyn_raw[];
+    // tensor copies land on 128-byte boundaries of shared memory
+    unsigned char* dyn = dyn_raw + ((128u - (smem_addr(dyn_raw) & 127u)) & 127u);
+    unsigned char* stage[2] = {dyn, dyn + Lay::BYTES};
+    const unsigned bar[2] = {smem_addr(dyn + Lay::OBAR), smem_addr(dyn + Lay::OBAR + 8)};
+    R* one = reinterpret_cast<R*>(dyn + Lay::OONE);
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        mbar_init(bar[0], 1);
+        mbar_init(bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const int first = blockIdx.x;
+    if (tid == 0 && first < ntiles && stage_interior(P, first % tiles_x, first / tiles_x))
+        stage_issue<N, Pr>(M, stage[0], bar[0], first % tiles_x, first / tiles_x);
+    unsigned phase = 0;   // bit b: parity of the next completion of stage b
+    int k = 0;
+    for (int t = first; t < ntiles; t += gridDim.x, ++k) {
+        const int b = k & 1;
+        const int bx = t % tiles_x, by = t / tiles_x;
+        const int nxt = t + gridDim.x;
+        const bool nxt_staged = nxt < ntiles && stage_interior(P, nxt % tiles_x, nxt / tiles_x);
+        if (tid == 0 && nxt_staged) stage_issue<N, Pr>(M, stage[b ^ 1], bar[b ^ 1], nxt % tiles_x, nxt / tiles_x);
+        if (stage_interior(P, bx, by)) {
+            const bool ok = mbar_wait(bar[b], (phase >> b) & 1u);
+            phase ^= 1u << b;
+            if (!__syncthreads_and(ok)) {
+                // give up: report, let the copy still in flight land, leave
+                if (tid == 0) {
+                    atomicExch(status, 1);
+                    if (nxt_staged) mbar_wait(bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+                }
+                __syncthreads();
+                return;
+            }
+            const StagedLoader<N, Pr> ld{P, stage[b]};
+            step_tile_l<N, STAGE_TX, STAGE_TY, true, Pr>(P, ld, pout_base, aout, ExportPtrs{}, bx, by, one);
+        } else {
+            step_tile<N, STAGE_TX, STAGE_TY, true, Pr>(P, pin_base, pout_base, ain, aout, ExportPtrs{}, bx, by, one);
+        }
+        __syncthreads();   // stage b and the one-cell tile free for reuse
+    }
+}
+
+}  // namespace lbm

@@ -62,13 +62,11 @@ __device__ __forceinline__ PopView<Pr> pop_view(const KParams& P, const void* ba
     return PopView<Pr>{(typename Pr::TR*)b, (typename Pr::TM*)(b + P.rest_elems * (long long)sizeof(typename Pr::TR))};
 }
 
-// Load population i of species s at cell c (dequantised to R).
+// A stored moving population (direction i >= 1) as a value of the arithmetic type R.
 template <class Pr, int KIND>
-__device__ __forceinline__ typename Pr::R ld_pop(const KParams& P, const PopView<Pr>& v, int s, int i, long long c, int site)
+__device__ __forceinline__ typename Pr::R dequant(const KParams& P, typename Pr::TM q, int i)
 {
     using R = typename Pr::R;
-    if (i == 0) return (R)LBM_LDX(Pr::COH, P, v.rest, (long long)s * P.S + c, P.rest_elems, site);
-    const auto q = LBM_LDX(Pr::COH, P, v.move, (long long)(s * 8 + i - 1) * P.S + c, P.move_elems, site);
     if constexpr (!Pr::QUANT) {
         return (R)q;
     } else {
@@ -78,6 +76,16 @@ __device__ __forceinline__ typename Pr::R ld_pop(const KParams& P, const PopView
         if (KIND == KIND_G) return qf * w;
         return qf * (w * P.f.E_ref);
     }
+}
+
+// Load population i of species s at cell c (dequantised to R).
+template <class Pr, int KIND>
+__device__ __forceinline__ typename Pr::R ld_pop(const KParams& P, const PopView<Pr>& v, int s, int i, long long c, int site)
+{
+    using R = typename Pr::R;
+    if (i == 0) return (R)LBM_LDX(Pr::COH, P, v.rest, (long long)s * P.S + c, P.rest_elems, site);
+    const auto q = LBM_LDX(Pr::COH, P, v.move, (long long)(s * 8 + i - 1) * P.S + c, P.move_elems, site);
+    return dequant<Pr, KIND>(P, q, i);
 }
 
 // The same load for a second read of a population in one step: through the cached
@@ -95,16 +103,7 @@ __device__ __forceinline__ typename Pr::R ld_pop_late(const KParams& P, const Po
     (void)site;
 #endif
     if (i == 0) return (R)lbm_ld_l1<Pr::COH>(v.rest + idx);
-    const auto q = lbm_ld_l1<Pr::COH>(v.move + idx);
-    if constexpr (!Pr::QUANT) {
-        return (R)q;
-    } else {
-        const float w = (float)wgt(i);
-        const float qf = to_f(q);
-        if (KIND == KIND_F) return qf * (w * F_SCALE);
-        if (KIND == KIND_G) return qf * w;
-        return qf * (w * P.f.E_ref);
-    }
+    return dequant<Pr, KIND>(P, lbm_ld_l1<Pr::COH>(v.move + idx), i);
 }
 
 // Store population i of species s at cell c (quantised from R).
@@ -129,6 +128,56 @@ __device__ __forceinline__ void st_pop(const KParams& P, const PopView<Pr>& v, i
         LBM_ST(P, v.move, idx, P.move_elems, site, from_f<TM>(q));
     }
 }
+
+// Where a step reads its inputs.  A loader addresses a cell of the tile-with-ring by a
+// Cell value and gives its populations (dequantised) and lagged values.
+//   GlobalLoader: the population and lagged sets in global memory, cells by their index in
+//     the lattice.  locate(lx, ly) maps a position of the tile-with-ring to a cell: periodic
+//     sides wrap (a full modulo, since a tile may be wider or taller than the lattice);
+//     other sides clamp, and the position is reported as beyond the lattice, to be filled
+//     by the ghost rule.  No address outside the planes is ever formed.
+//   StagedLoader: the same inputs of one interior tile copied into shared memory by the
+//     tensor-memory accelerator (lbm_staged.cuh); cells by their position in the tile.
+template <class Pr>
+struct GlobalLoader {
+    using R = typename Pr::R;
+    using Cell = long long;
+    const KParams& P;
+    PopView<Pr> pin;
+    const typename Pr::TA* __restrict__ ain;
+    int x0, y0;        // lattice position of the tile's first cell
+    bool xper, yper;
+    __device__ __forceinline__ bool locate(int lx, int ly, Cell& cell) const
+    {
+        int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        bool beyond = false;
+        if (gx < 0 || gx >= P.nx) {
+            if (xper) gx = wrap_index(gx, P.nx);
+            else { beyond = true; gx = min(max(gx, 0), P.nx - 1); }
+        }
+        if (gy < 0 || gy >= P.ny) {
+            if (yper) gy = wrap_index(gy, P.ny);
+            else { beyond = true; gy = min(max(gy, 0), P.ny - 1); }
+        }
+        cell = (long long)gy * P.nx + gx;
+        return !beyond;
+    }
+    __device__ __forceinline__ Cell own(int x, int y, int, int) const { return (long long)y * P.nx + x; }
+    template <int KIND>
+    __device__ __forceinline__ R pop(int s, int i, Cell c, int site) const
+    {
+        return ld_pop<Pr, KIND>(P, pin, s, i, c, site);
+    }
+    template <int KIND>
+    __device__ __forceinline__ R pop_late(int s, int i, Cell c, int site) const
+    {
+        return ld_pop_late<Pr, KIND>(P, pin, s, i, c, site);
+    }
+    __device__ __forceinline__ R aux(int a, Cell c, int site) const
+    {
+        return (R)LBM_LDX(Pr::COH, P, ain, a * P.S + c, P.aux_elems, site);
+    }
+};
 
 // eq. H for one cell: f_l (and T when WANT_T) from rho H and phi_p, in FP64.  Policies
 // that compute in FP32 screen the cell in FP32 first: where rho H lies above the
@@ -211,26 +260,24 @@ __device__ __forceinline__ void map_cell(const KParams& P, const typename Pr::R 
 }
 
 // Stage A + B for a halo cell: phi_p, rho and psi only (the map in FP64).
-template <int N, class Pr>
-__device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>& pin,
-                                             const typename Pr::TA* __restrict__ ain, long long c,
-                                             typename Pr::R (&phi)[N], typename Pr::R& rho, typename Pr::R& psi)
+template <int N, class Pr, class L>
+__device__ __forceinline__ void halo_moments_l(const KParams& P, const L& ld, typename L::Cell c,
+                                               typename Pr::R (&phi)[N], typename Pr::R& rho, typename Pr::R& psi)
 {
     using R = typename Pr::R;
-    const long long S = P.S;
-    const R mdm = (R)LBM_LDX(Pr::COH, P, ain, aux_mdot() * S + c, P.aux_elems, 1);
-    const R Qm = (R)LBM_LDX(Pr::COH, P, ain, aux_Q() * S + c, P.aux_elems, 2);
+    const R mdm = ld.aux(aux_mdot(), c, 1);
+    const R Qm = ld.aux(aux_Q(), c, 2);
     const R iden = R(1) / (R(1) - R(0.5) * mdm);
 #pragma unroll
     for (int p = 0; p < N; ++p) {
         R s = R(0);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s += ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 3);
+        for (int i = 0; i < 9; ++i) s += ld.template pop<KIND_G>(1 + p, i, c, 3);
         phi[p] = s * iden;
     }
     R sh = R(0);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 4);
+    for (int i = 0; i < 9; ++i) sh += ld.template pop<KIND_H>(N + 1, i, c, 4);
     const R rhoH = rfma(R(0.5), Qm, sh);
     // eq. H (f_l as the FP64 map gives it); the rest of eq. 2 in R
     R fl, T;
@@ -240,33 +287,39 @@ __device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>
     rho = rfma(fs, mix_sum<N, R>(phi, C.rho_s), fl * mix_sum<N, R>(phi, C.rho_l));
     psi = fs * mix_sum<N, R>(phi, C.drho);
 }
+template <int N, class Pr>
+__device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>& pin,
+                                             const typename Pr::TA* __restrict__ ain, long long c,
+                                             typename Pr::R (&phi)[N], typename Pr::R& rho, typename Pr::R& psi)
+{
+    const GlobalLoader<Pr> ld{P, pin, ain, 0, 0, false, false};
+    halo_moments_l<N, Pr>(P, ld, c, phi, rho, psi);
+}
 
 // Stage A + B of one cell of the tile or its ring: phi_p, rho H, f_l, T, rho and psi.
 // f_l is the FP64 map's (map_cell), the rest of eq. 2 runs in R.  T is needed only for the tile's own
 // cells, but almost every warp holds both kinds, so it is computed for all (a branch on
 // the kind would run both versions of the map).
-template <int N, class Pr>
-__device__ __forceinline__ void cell_moments(const KParams& P, const PopView<Pr>& pin,
-                                             const typename Pr::TA* __restrict__ ain, long long c,
-                                             typename Pr::R (&phi)[N], typename Pr::R& rhoH, typename Pr::R& fl,
-                                             typename Pr::R& T, typename Pr::R& rho, typename Pr::R& psi)
+template <int N, class Pr, class L>
+__device__ __forceinline__ void cell_moments_l(const KParams& P, const L& ld, typename L::Cell c,
+                                               typename Pr::R (&phi)[N], typename Pr::R& rhoH, typename Pr::R& fl,
+                                               typename Pr::R& T, typename Pr::R& rho, typename Pr::R& psi)
 {
     using R = typename Pr::R;
     using K = exact_t<R>;
-    const long long S = P.S;
-    const R mdm = (R)LBM_LDX(Pr::COH, P, ain, aux_mdot() * S + c, P.aux_elems, 1);
-    const R Qm = (R)LBM_LDX(Pr::COH, P, ain, aux_Q() * S + c, P.aux_elems, 2);
+    const R mdm = ld.aux(aux_mdot(), c, 1);
+    const R Qm = ld.aux(aux_Q(), c, 2);
     const R iden = R(1) / (R(1) - K(0.5) * mdm);
 #pragma unroll
     for (int p = 0; p < N; ++p) {
         R s = R(0);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s += ld_pop<Pr, KIND_G>(P, pin, 1 + p, i, c, 3);
+        for (int i = 0; i < 9; ++i) s += ld.template pop<KIND_G>(1 + p, i, c, 3);
         phi[p] = s * iden;
     }
     R sh = R(0);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) sh += ld_pop<Pr, KIND_H>(P, pin, N + 1, i, c, 4);
+    for (int i = 0; i < 9; ++i) sh += ld.template pop<KIND_H>(N + 1, i, c, 4);
     rhoH = rfma(K(0.5), Qm, sh);
     map_cell<N, Pr, true>(P, phi, rhoH, fl, T);
     const Coef<R>& C = coef<R>(P);
@@ -387,11 +440,10 @@ __host__ __device__ constexpr int tile_smem_elems()
 // TX * TY threads; smem holds tile_smem_elems<N, TX, TY, Pr>() elements of shared memory.
 // Every thread of the block must call it (it holds two block barriers); the caller
 // places a block barrier before smem is used again.
-template <int N, int TX, int TY, bool COLLIDE, class Pr>
-__device__ __forceinline__ void step_tile(const KParams& P, const void* __restrict__ pin_base,
-                                          void* __restrict__ pout_base, const typename Pr::TA* __restrict__ ain,
-                                          typename Pr::TA* __restrict__ aout, const ExportPtrs& ex, int bx, int by,
-                                          typename Pr::R* smem)
+template <int N, int TX, int TY, bool COLLIDE, class Pr, class L>
+__device__ __forceinline__ void step_tile_l(const KParams& P, const L& ld, void* __restrict__ pout_base,
+                                            typename Pr::TA* __restrict__ aout, const ExportPtrs& ex, int bx, int by,
+                                            typename Pr::R* smem)
 {
     using R = typename Pr::R;
     using K = exact_t<R>;
@@ -410,28 +462,13 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     const int x = x0 + tx, y = y0 + ty;
     const bool owned = x < nx && y < ny;
     const bool xper = P.bc[0] == PERIODIC, yper = P.bc[2] == PERIODIC;
-    const PopView<Pr> pin = pop_view<Pr>(P, pin_base);
     const Coef<R>& C = coef<R>(P);
+    using Cell = typename L::Cell;
 
-    // Position (lx, ly) of the tile-with-ring as a cell of the lattice.  The coordinates
-    // are brought into range before anything else (periodic: full modulo, since a tile may
-    // be wider / taller than the domain; otherwise clamped, and the position is reported as
-    // beyond the domain, to be filled by the ghost rule), so no address outside the planes
-    // is ever formed.
-    auto locate = [&](int lx, int ly, long long& cell) {
-        int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        bool beyond = false;
-        if (gx < 0 || gx >= nx) {
-            if (xper) gx = wrap_index(gx, nx);
-            else { beyond = true; gx = min(max(gx, 0), nx - 1); }
-        }
-        if (gy < 0 || gy >= ny) {
-            if (yper) gy = wrap_index(gy, ny);
-            else { beyond = true; gy = min(max(gy, 0), ny - 1); }
-        }
-        cell = (long long)gy * nx + gx;
-        return !beyond;
-    };
+    // Position (lx, ly) of the tile-with-ring as a cell of the loader (GlobalLoader: brought
+    // into range before anything else, so no address outside the planes is ever formed; a
+    // position beyond a non-periodic side is reported, to be filled by the ghost rule).
+    auto locate = [&](int lx, int ly, Cell& cell) { return ld.locate(lx, ly, cell); };
     R phi[N], rhoH, fl, T, rho, psi, mu, lam, cp, chi;
     if constexpr (Pr::COMPACT) {
         // ---- stages A + B: one code path for all (TX + 2)(TY + 2) positions, so that
@@ -439,10 +476,10 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
 #pragma unroll 1
         for (int k = tid; k < W * H; k += NT) {
             const int lx = k % W, ly = k / W;
-            long long cell;
+            Cell cell;
             if (!locate(lx, ly, cell)) continue;
             R ph[N], rH, flv, Tv, r, ps;
-            cell_moments<N, Pr>(P, pin, ain, cell, ph, rH, flv, Tv, r, ps);
+            cell_moments_l<N, Pr>(P, ld, cell, ph, rH, flv, Tv, r, ps);
 #pragma unroll
             for (int p = 0; p < N; ++p) s_phi[p][ly][lx] = ph[p];
             s_rho[ly][lx] = r;
@@ -459,17 +496,17 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         // ---- stages A + B: the own cell in registers (the rest of eq. 2 as well),
         // then the ring, phi_p, rho and psi only -----------------------------------
         auto halo_at = [&](int lx, int ly) {
-            long long cell;
+            Cell cell;
             if (!locate(lx, ly, cell)) return;
             R ph[N], r, ps;
-            halo_moments<N, Pr>(P, pin, ain, cell, ph, r, ps);
+            halo_moments_l<N, Pr>(P, ld, cell, ph, r, ps);
 #pragma unroll
             for (int p = 0; p < N; ++p) s_phi[p][ly][lx] = ph[p];
             s_rho[ly][lx] = r;
             s_psi[ly][lx] = ps;
         };
         if (owned) {
-            cell_moments<N, Pr>(P, pin, ain, (long long)y * nx + x, phi, rhoH, fl, T, rho, psi);
+            cell_moments_l<N, Pr>(P, ld, ld.own(x, y, tx, ty), phi, rhoH, fl, T, rho, psi);
             const R fs = R(1) - fl;
             mu = rfma(fs, mix_sum<N, R>(phi, C.mu_s), fl * mix_sum<N, R>(phi, C.mu_l));
             lam = rfma(fs, mix_sum<N, R>(phi, C.lam_s), fl * mix_sum<N, R>(phi, C.lam_l));
@@ -532,7 +569,8 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     if (!owned) return;
 
     const int lx = tx + 1, ly = ty + 1;
-    const long long c = (long long)y * nx + x;
+    const long long c = (long long)y * nx + x;   // stores: lattice index
+    const Cell oc = ld.own(x, y, tx, ty);        // loads of the own cell
     if constexpr (Pr::COMPACT) {
         // ---- own cell: the rest of eq. 2 ---------------------------------------
 #pragma unroll
@@ -623,7 +661,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     // ---- stage E: flow macroscopics ----------------------------------------
     R f[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = ld_pop_late<Pr, KIND_F>(P, pin, 0, i, c, 5);
+    for (int i = 0; i < 9; ++i) f[i] = ld.template pop_late<KIND_F>(0, i, oc, 5);
     const R jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
     const R jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
     const R sum_f = ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
@@ -639,7 +677,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     const R usx = rfma(K(0.5), Fx, jx) * irho, usy = rfma(K(0.5), Fy, jy) * irho;
     const R fpx = chi * (C.us[0] - usx), fpy = chi * (C.us[1] - usy);
     const R ux = rfma(K(0.5), fpx, usx), uy = rfma(K(0.5), fpy, usy);
-    const R psim = (R)LBM_LDX(Pr::COH, P, ain, aux_psi() * S + c, P.aux_elems, 14);
+    const R psim = ld.aux(aux_psi(), oc, 14);
     const R mdot = -((psi - psim) + (ux * gsx + uy * gsy)) * irho;
     const R Ssrc = rfma(rho, mdot, ux * grx + uy * gry);
     const R Lxx = rfma(K(2) * ux, Fx, Ssrc * R(1.0 / 3.0));
@@ -701,9 +739,9 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         for (int pp = 0; pp < N; ++pp) {
             R gq[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) gq[i] = ld_pop_late<Pr, KIND_G>(P, pin, 1 + pp, i, c, 6);
-            const R Dx = phi[pp] * ux - (R)LBM_LDX(Pr::COH, P, ain, aux_phiux(pp) * S + c, P.aux_elems, 15);
-            const R Dy = phi[pp] * uy - (R)LBM_LDX(Pr::COH, P, ain, aux_phiuy(N, pp) * S + c, P.aux_elems, 16);
+            for (int i = 0; i < 9; ++i) gq[i] = ld.template pop_late<KIND_G>(1 + pp, i, oc, 6);
+            const R Dx = phi[pp] * ux - ld.aux(aux_phiux(pp), oc, 15);
+            const R Dy = phi[pp] * uy - ld.aux(aux_phiuy(N, pp), oc, 16);
             const R b0 = og * phi[pp] + kg * phi[pp] * mdot;
             const R bxv = K(3) * og * phi[pp] * ux + kg * rfma(K(3), Dx, Rx[pp]);
             const R byv = K(3) * og * phi[pp] * uy + kg * rfma(K(3), Dy, Ry[pp]);
@@ -727,7 +765,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     {
         R h[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) h[i] = ld_pop_late<Pr, KIND_H>(P, pin, N + 1, i, c, 7);
+        for (int i = 0; i < 9; ++i) h[i] = ld.template pop_late<KIND_H>(N + 1, i, oc, 7);
         const R Z = rho * cp * T, E = C.E_ref * T;
         const R kh = rfma(K(-0.5), oh, R(1)), oh1 = R(1) - oh;
         const R Zm = Z * mdot;
@@ -777,6 +815,18 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
         LBM_ST(P, aout, aux_Q() * S + c, P.aux_elems, 33, (TA)Zm);
         LBM_ST(P, aout, aux_psi() * S + c, P.aux_elems, 34, (TA)psi);
     }
+}
+
+// One TX x TY tile read from global memory (the loader of the one-cell step).
+template <int N, int TX, int TY, bool COLLIDE, class Pr>
+__device__ __forceinline__ void step_tile(const KParams& P, const void* __restrict__ pin_base,
+                                          void* __restrict__ pout_base, const typename Pr::TA* __restrict__ ain,
+                                          typename Pr::TA* __restrict__ aout, const ExportPtrs& ex, int bx, int by,
+                                          typename Pr::R* smem)
+{
+    const GlobalLoader<Pr> ld{P, pop_view<Pr>(P, pin_base), ain, bx * TX, by * TY, P.bc[0] == PERIODIC,
+                              P.bc[2] == PERIODIC};
+    step_tile_l<N, TX, TY, COLLIDE, Pr>(P, ld, pout_base, aout, ex, bx, by, smem);
 }
 
 // One launch = one time step of one lattice, one block per tile.

@@ -108,6 +108,7 @@ def library():
             lib.lbm_get_steps.argtypes = [_VP]
             lib.lbm_get_steps.restype = ctypes.c_longlong
             lib.lbm_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+            lib.lbm_set_staging.argtypes = [_VP, ctypes.c_int]
             lib.lbm_debug_bounds.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong)]
             lib.lbm_debug_bounds.restype = ctypes.c_int
             lib.lbm_last_error.argtypes = [_VP]
@@ -136,7 +137,7 @@ def library():
             lib.lbm_batch_last_error.restype = ctypes.c_char_p
             lib.lbm_batch_destroy.argtypes = [_VP]
             for name in ("lbm_create", "lbm_set_stream", "lbm_set_fields", "lbm_step", "lbm_get_fields",
-                         "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile",
+                         "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile", "lbm_set_staging",
                          "lbm_measure_fp64_rate", "lbm_slab_create", "lbm_slab_geometry", "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_sums",
                          "lbm_batch_create", "lbm_batch_set_stream", "lbm_batch_set_plan", "lbm_batch_get_plan",
                          "lbm_batch_step", "lbm_batch_sync", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_adjoint_fl_loss"):
@@ -263,6 +264,10 @@ def lbm_set_tile(h, bx, by):
     return _check(library().lbm_set_tile(h, bx, by), h)
 
 
+def lbm_set_staging(h, on):
+    return _check(library().lbm_set_staging(h, 1 if on else 0), h)
+
+
 def lbm_debug_bounds(h):
     out = (ctypes.c_longlong * 3)()
     _check(library().lbm_debug_bounds(h, out), h)
@@ -361,7 +366,7 @@ def make_structs(case, precision="fp64", diag_every=0):
 class Solver:
     """One solver handle on the current CUDA device, fed from a ``workloads.Case``."""
 
-    def __init__(self, case, precision="fp64", diag_every=0, tile=None, stream=None):
+    def __init__(self, case, precision="fp64", diag_every=0, tile=None, stream=None, staged=False):
         import torch
         self.torch = torch
         self.case = case
@@ -373,6 +378,8 @@ class Solver:
         lbm_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream))
         if tile is not None:
             lbm_set_tile(self.h, *tile)
+        if staged:
+            lbm_set_staging(self.h, True)
 
     def set_fields(self, phi=None, T=None, ux=None, uy=None):
         """Initial state from device tensors (default: the case's own fields)."""
