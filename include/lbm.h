@@ -199,7 +199,9 @@ int lbm_set_tile(lbm_handle* h, int bx, int by);
  * cell); tiles that touch a side of the lattice are stepped from global memory.  A
  * service of the library for LBM_FP16S and LBM_BF16S handles with N = 2, nx a multiple of 8
  * and the 32x8 tile; LBM_EINVAL otherwise, LBM_ECUDA when the tensor maps cannot be
- * encoded.  on = 0 returns to the one-launch-per-step form.  Every wait for a copy is
+ * encoded.  on = 1: the persistent double-buffered form; on = 2: one tile per block (a grid of
+ * all tiles, up to four blocks per SM, each waiting for its own copies); on = 0 returns to
+ * the one-launch-per-step form.  Every wait for a copy is
  * bounded; a wait that gave up is reported as LBM_ETIMEOUT by the next lbm_step with
  * diag_every > 0 or lbm_get_diagnostics, with the state undefined. */
 int lbm_set_staging(lbm_handle* h, int on);

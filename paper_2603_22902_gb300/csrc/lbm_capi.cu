@@ -308,8 +308,9 @@ int lbm_set_tile(lbm_handle* h, int bx, int by)
 int lbm_set_staging(lbm_handle* h, int on)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
+    if (on < 0 || on > 2) return fail(h, LBM_EINVAL, "staging mode must be 0, 1 or 2");
     if (!on) {
-        h->staged = false;
+        h->staged = 0;
         return LBM_OK;
     }
     if ((h->precision != LBM_FP16S && h->precision != LBM_BF16S) || h->N != 2)
@@ -327,7 +328,7 @@ int lbm_set_staging(lbm_handle* h, int on)
         ok = h->precision == LBM_FP16S ? encode_stage_maps<2, PrecFP16S>(h, k, h->stage_maps[k])
                                        : encode_stage_maps<2, PrecBF16S>(h, k, h->stage_maps[k]);
     if (!ok) return fail(h, LBM_ECUDA, "tensor maps of the staged step could not be encoded");
-    h->staged = true;
+    h->staged = on;
     return LBM_OK;
 }
 
@@ -404,7 +405,7 @@ int lbm_step(lbm_handle* h, long nsteps)
             if (h->staged)
                 return launch_staged<decltype(n)::value, decltype(pr)>(h->P, h->stage_maps[a], h->pop[a], h->pop[b],
                                                                        h->aux[a], h->aux[b], h->stage_status, h->sms,
-                                                                       h->stream);
+                                                                       h->staged, h->stream);
             return launch_step<decltype(n)::value, decltype(pr)>(h->P, h->pop[a], h->pop[b], h->aux[a], h->aux[b],
                                                                  h->tile, h->stream);
         });

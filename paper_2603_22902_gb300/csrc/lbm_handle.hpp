@@ -28,7 +28,7 @@ struct lbm_handle {
     long long steps = 0;
     cudaStream_t stream = nullptr;
     // TMA-staged step (lbm_set_staging): tensor maps of both population sets, status word
-    bool staged = false;
+    int staged = 0;                       // 0 off, 1 persistent double-buffered, 2 one tile per block
     lbm::StageMaps stage_maps[2];
     int* stage_status = nullptr;
     int sms = 0;

@@ -40,9 +40,10 @@ cudaError_t launch_init(const KParams& P, const double* phi, const double* T, co
 struct StageMaps {
     CUtensorMap m[6];   // boxes A..F of lbm_staged.cuh
 };
+// mode 1: persistent grid, double-buffered stages; mode 2: one tile per block.
 template <int N, class Pr>
 cudaError_t launch_staged(const KParams& P, const StageMaps& maps, const void* pin, void* pout, const void* ain,
-                          void* aout, int* status, int sms, cudaStream_t st);
+                          void* aout, int* status, int sms, int mode, cudaStream_t st);
 template <class Pr>
 constexpr bool staged_policy()
 {

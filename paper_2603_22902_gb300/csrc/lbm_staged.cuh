@@ -55,6 +55,8 @@ struct StageLayout {
     static constexpr int SMEM_ONE = tile_smem_elems<N, STAGE_TX, STAGE_TY, Pr>() * (int)sizeof(typename Pr::R);
     // (TOTAL has 128 bytes of slack: the kernel aligns its base to 128 bytes)
     static constexpr int OBAR = 2 * BYTES, OONE = OBAR + 128, TOTAL = OONE + stage_round(SMEM_ONE) + 128;
+    // one stage (one tile per block)
+    static constexpr int OBAR1 = BYTES, OONE1 = OBAR1 + 128, TOTAL1 = OONE1 + stage_round(SMEM_ONE) + 128;
 };
 
 // Reads of one staged interior tile; a cell is (lx, ly) of the tile with its ring.
@@ -218,6 +220,46 @@ staged_step_kernel(const KParams P, const __grid_constant__ StageMaps M, const v
         }
         __syncthreads();   // stage b and the one-cell tile free for reuse
     }
+}
+
+// The same staging with one tile per block (a grid of all tiles, up to four blocks per SM):
+// thread 0 issues the tile's six copies, every thread waits for them, and the tile is
+// computed from the staged copy; tiles that touch a side run the one-cell step.
+template <int N, class Pr>
+__global__ void __launch_bounds__(STAGE_NT, 4)
+staged_tile_kernel(const KParams P, const __grid_constant__ StageMaps M, const void* __restrict__ pin_base,
+                   void* __restrict__ pout_base, const typename Pr::TA* __restrict__ ain,
+                   typename Pr::TA* __restrict__ aout, int* __restrict__ status)
+{
+    using Lay = StageLayout<N, Pr>;
+    using R = typename Pr::R;
+    extern __shared__ __align__(128) unsigned char dyn_raw[];
+    unsigned char* dyn = dyn_raw + ((128u - (smem_addr(dyn_raw) & 127u)) & 127u);
+    R* one = reinterpret_cast<R*>(dyn + Lay::OONE1);
+    const int bx = blockIdx.x, by = blockIdx.y;
+    if (!stage_interior(P, bx, by)) {
+        step_tile<N, STAGE_TX, STAGE_TY, true, Pr>(P, pin_base, pout_base, ain, aout, ExportPtrs{}, bx, by, one);
+        return;
+    }
+    const unsigned bar = smem_addr(dyn + Lay::OBAR1);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        stage_issue<N, Pr>(M, dyn, bar, bx, by);
+    }
+    __syncthreads();   // the mbarrier is initialised before anyone waits on it
+    const bool ok = mbar_wait(bar, 0);
+    if (!__syncthreads_and(ok)) {
+        // give up: report, let the copy still in flight land, leave
+        if (threadIdx.x == 0) {
+            atomicExch(status, 1);
+            mbar_wait(bar, 0);
+        }
+        __syncthreads();
+        return;
+    }
+    const StagedLoader<N, Pr> ld{P, dyn};
+    step_tile_l<N, STAGE_TX, STAGE_TY, true, Pr>(P, ld, pout_base, aout, ExportPtrs{}, bx, by, one);
 }
 
 }  // namespace lbm

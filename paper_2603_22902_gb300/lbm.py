@@ -264,8 +264,8 @@ def lbm_set_tile(h, bx, by):
     return _check(library().lbm_set_tile(h, bx, by), h)
 
 
-def lbm_set_staging(h, on):
-    return _check(library().lbm_set_staging(h, 1 if on else 0), h)
+def lbm_set_staging(h, mode):
+    return _check(library().lbm_set_staging(h, int(mode)), h)
 
 
 def lbm_debug_bounds(h):
@@ -379,7 +379,7 @@ class Solver:
         if tile is not None:
             lbm_set_tile(self.h, *tile)
         if staged:
-            lbm_set_staging(self.h, True)
+            lbm_set_staging(self.h, int(staged))
 
     def set_fields(self, phi=None, T=None, ux=None, uy=None):
         """Initial state from device tensors (default: the case's own fields)."""

@@ -1,6 +1,7 @@
-"""The TMA-staged form of the step (lbm_set_staging; FP16 and BF16 storage, N = 2): a
-persistent grid copies each interior tile's inputs into shared memory with tensor copies
-while it computes the previous tile.  It runs the arithmetic of the one-launch form cell by
+"""The TMA-staged forms of the step (lbm_set_staging; FP16 and BF16 storage, N = 2): each
+interior tile's inputs are copied into shared memory by tensor copies, either by a
+persistent grid that copies the next tile while it computes the current one (mode 1) or by
+one block per tile (mode 2).  It runs the arithmetic of the one-launch form cell by
 cell, so the two forms must agree to the rounding of contractions, and the staged form
 must hold the one-launch form's bounds against the CPU oracle."""
 import numpy as np
@@ -46,14 +47,15 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_staged_equals_one_launch_form(lbm, prec, name):
+def test_staged_equals_one_launch_form(lbm, prec, name, mode):
     case = CASES[name]()
     if name == "sessile_cap_160x64_walls":
         case.bc = (W.WALL, W.WALL, W.WALL, W.WALL)
-    A, da = run(lbm, case, prec, False, 300)
-    B, db = run(lbm, case, prec, True, 300)
+    A, da = run(lbm, case, prec, 0, 300)
+    B, db = run(lbm, case, prec, mode, 300)
     errs = {k: float(np.abs(A[k] - B[k]).max()) for k in FIELDS}
     print(name, prec, errs)
     assert errs["phi"] <= 1e-6 and errs["fl"] <= 1e-6 and errs["ux"] <= 1e-8 and errs["uy"] <= 1e-8, errs
@@ -62,10 +64,11 @@ def test_staged_equals_one_launch_form(lbm, prec, name):
         assert abs(da["mass"][p] - db["mass"][p]) <= 1e-9 * max(1.0, da["mass"][p])
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
-def test_staged_against_oracle(lbm, prec):
+def test_staged_against_oracle(lbm, prec, mode):
     case = W.sessile_cap(96, 48, 14.0, theta=70.0, ste=0.2, T_wall=-1.5)
-    G, _ = run(lbm, case, prec, True, 200)
+    G, _ = run(lbm, case, prec, mode, 200)
     O = oracle.Oracle(case).step(200).fields()
     errs = {k: float(np.abs(G[k] - O[k]).max()) for k in BOUNDS[prec]}
     print(prec, errs)
@@ -73,10 +76,11 @@ def test_staged_against_oracle(lbm, prec):
         assert errs[k] <= b, (k, errs[k], b)
 
 
-def test_staged_sessile_drop_512(lbm):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_staged_sessile_drop_512(lbm, mode):
     case = W.sessile_drop()
-    A, da = run(lbm, case, "fp16s", False, 2000)
-    B, db = run(lbm, case, "fp16s", True, 2000)
+    A, da = run(lbm, case, "fp16s", 0, 2000)
+    B, db = run(lbm, case, "fp16s", mode, 2000)
     fa, fb = front_height(A, case.nx), front_height(B, case.nx)
     print("front one-launch", fa, "staged", fb, "max |dphi|", float(np.abs(A["phi"] - B["phi"]).max()))
     assert abs(fa - fb) <= 1e-3
@@ -89,5 +93,5 @@ def test_staging_refused_where_not_compiled(lbm):
                        ("fp16s", W.compound_drop(n=96, R_core=10.0, R_shell=20.0, ny=64)),
                        ("fp16s", W.sessile_drop(n=90, R=20.0, ny=64))):
         with pytest.raises(lbm.LBMError) as e:
-            lbm.Solver(case, precision=prec, staged=True)
+            lbm.Solver(case, precision=prec, staged=2)
         assert e.value.code == lbm.LBM_EINVAL
