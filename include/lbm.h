@@ -192,18 +192,18 @@ int lbm_debug_bounds(lbm_handle* h, long long* out3);
 int lbm_set_tile(lbm_handle* h, int bx, int by);
 
 
-/* Step with its inputs staged in shared memory by the tensor-memory accelerator: a
- * persistent grid of two blocks per SM, each copying the next interior 32x8 tile's
- * populations and lagged values (tile and ring) into one half of a double buffer while it
- * computes the current tile from the other (the arithmetic is that of lbm_step, cell by
- * cell); tiles that touch a side of the lattice are stepped from global memory.  A
- * service of the library for LBM_FP16S and LBM_BF16S handles with N = 2, nx a multiple of 8
- * and the 32x8 tile; LBM_EINVAL otherwise, LBM_ECUDA when the tensor maps cannot be
- * encoded.  on = 1: the persistent double-buffered form; on = 2: one tile per block (a grid of
- * all tiles, up to four blocks per SM, each waiting for its own copies); on = 0 returns to
- * the one-launch-per-step form.  Every wait for a copy is
- * bounded; a wait that gave up is reported as LBM_ETIMEOUT by the next lbm_step with
- * diag_every > 0 or lbm_get_diagnostics, with the state undefined. */
+/* Step with its inputs staged in shared memory by the tensor-memory accelerator: one
+ * block per 32x8 tile, whose thread 0 copies the tile's populations and lagged values
+ * (tile and ring) with six tensor copies; the tile is then computed from shared memory
+ * (the arithmetic is that of lbm_step, cell by cell, bit for bit); tiles that touch a
+ * side of the lattice are stepped from global memory.  A service of the library for
+ * LBM_FP16S and LBM_BF16S handles with N = 2, nx a multiple of 8 and the 32x8 tile, where
+ * it is on from lbm_create (a handle whose tensor maps cannot be encoded runs the
+ * one-launch form).  on = 0 returns to the one-launch form, on = 1 asks for the staged one
+ * (LBM_EINVAL where it does not apply, LBM_ECUDA when the tensor maps cannot be encoded);
+ * lbm_set_tile with another shape turns it off.  Every wait for the copies is bounded; a
+ * wait that gave up is reported as LBM_ETIMEOUT by the next lbm_step with diag_every > 0
+ * or lbm_get_diagnostics, with the state undefined. */
 int lbm_set_staging(lbm_handle* h, int on);
 
 /* Diagnostics sums without any allocation, for callers that cannot allocate device

@@ -136,6 +136,30 @@ static bool encode_stage_maps(lbm_handle* h, int k, StageMaps& M)
            encode_map(&M.m[5], aux, Lay::EA, nx, ny, 3 + 2 * N, STAGE_TX, STAGE_TY, 1 + 2 * N);
 }
 
+// Turn the staged step on where the handle allows it (see lbm_set_staging); with report,
+// the reason it does not apply goes to lbm_last_error.
+static int enable_staging(lbm_handle* h, bool report)
+{
+    if ((h->precision != LBM_FP16S && h->precision != LBM_BF16S) || h->N != 2)
+        return report ? fail(h, LBM_EINVAL, "the staged step is compiled for LBM_FP16S and LBM_BF16S with N = 2")
+                      : LBM_EINVAL;
+    if (h->nx % 8 != 0)
+        return report ? fail(h, LBM_EINVAL, "the staged step needs nx a multiple of 8 (16-byte rows)") : LBM_EINVAL;
+    if (h->tile != TILE_32x8) return report ? fail(h, LBM_EINVAL, "the staged step uses the 32x8 tile") : LBM_EINVAL;
+    LBM_CUDA_TRY(h, cudaSetDevice(h->device));
+    if (!h->stage_status) {
+        LBM_CUDA_TRY(h, cudaMalloc(&h->stage_status, sizeof(int)));
+        LBM_CUDA_TRY(h, cudaMemset(h->stage_status, 0, sizeof(int)));
+    }
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k)
+        ok = h->precision == LBM_FP16S ? encode_stage_maps<2, PrecFP16S>(h, k, h->stage_maps[k])
+                                       : encode_stage_maps<2, PrecBF16S>(h, k, h->stage_maps[k]);
+    if (!ok) return report ? fail(h, LBM_ECUDA, "tensor maps of the staged step could not be encoded") : LBM_ECUDA;
+    h->staged = true;
+    return LBM_OK;
+}
+
 extern "C" {
 
 int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_thermal* th, const lbm_bc* bc,
@@ -273,6 +297,9 @@ int lbm_create(const lbm_grid* grid, int N, const lbm_phase* phases, const lbm_t
         delete h;
         return fail(nullptr, LBM_ENOMEM, "device allocation failed");
     }
+    // the TMA-staged step is the default where it applies (it computes every cell as the
+    // one-launch form does, bit for bit)
+    if (enable_staging(h, false) != LBM_OK) cudaGetLastError();
     *out = h;
     return LBM_OK;
 }
@@ -297,7 +324,7 @@ int lbm_set_tile(lbm_handle* h, int bx, int by)
         if (tx == bx && ty == by) {
             if (h->precision == LBM_DF64 && id != TILE_32x8)
                 return fail(h, LBM_EINVAL, "the LBM_DF64 policy is compiled for the 32x8 tile only");
-            if (h->staged && id != TILE_32x8) return fail(h, LBM_EINVAL, "the staged step uses the 32x8 tile");
+            if (id != TILE_32x8) h->staged = false;  // the staged step is compiled for 32x8
             h->tile = id;
             return LBM_OK;
         }
@@ -308,28 +335,11 @@ int lbm_set_tile(lbm_handle* h, int bx, int by)
 int lbm_set_staging(lbm_handle* h, int on)
 {
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
-    if (on < 0 || on > 2) return fail(h, LBM_EINVAL, "staging mode must be 0, 1 or 2");
     if (!on) {
-        h->staged = 0;
+        h->staged = false;
         return LBM_OK;
     }
-    if ((h->precision != LBM_FP16S && h->precision != LBM_BF16S) || h->N != 2)
-        return fail(h, LBM_EINVAL, "the staged step is compiled for LBM_FP16S and LBM_BF16S with N = 2");
-    if (h->nx % 8 != 0) return fail(h, LBM_EINVAL, "the staged step needs nx a multiple of 8 (16-byte rows)");
-    if (h->tile != TILE_32x8) return fail(h, LBM_EINVAL, "the staged step uses the 32x8 tile");
-    LBM_CUDA_TRY(h, cudaSetDevice(h->device));
-    if (!h->sms) LBM_CUDA_TRY(h, cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
-    if (!h->stage_status) {
-        LBM_CUDA_TRY(h, cudaMalloc(&h->stage_status, sizeof(int)));
-        LBM_CUDA_TRY(h, cudaMemset(h->stage_status, 0, sizeof(int)));
-    }
-    bool ok = true;
-    for (int k = 0; k < 2 && ok; ++k)
-        ok = h->precision == LBM_FP16S ? encode_stage_maps<2, PrecFP16S>(h, k, h->stage_maps[k])
-                                       : encode_stage_maps<2, PrecBF16S>(h, k, h->stage_maps[k]);
-    if (!ok) return fail(h, LBM_ECUDA, "tensor maps of the staged step could not be encoded");
-    h->staged = on;
-    return LBM_OK;
+    return enable_staging(h, true);
 }
 
 int lbm_set_fields(lbm_handle* h, const double* phi, const double* T, const double* ux, const double* uy, int where)
@@ -404,8 +414,8 @@ int lbm_step(lbm_handle* h, long nsteps)
         cudaError_t e = dispatch(h->N, h->precision, [&](auto n, auto pr) {
             if (h->staged)
                 return launch_staged<decltype(n)::value, decltype(pr)>(h->P, h->stage_maps[a], h->pop[a], h->pop[b],
-                                                                       h->aux[a], h->aux[b], h->stage_status, h->sms,
-                                                                       h->staged, h->stream);
+                                                                       h->aux[a], h->aux[b], h->stage_status,
+                                                                       h->stream);
             return launch_step<decltype(n)::value, decltype(pr)>(h->P, h->pop[a], h->pop[b], h->aux[a], h->aux[b],
                                                                  h->tile, h->stream);
         });

@@ -28,10 +28,9 @@ struct lbm_handle {
     long long steps = 0;
     cudaStream_t stream = nullptr;
     // TMA-staged step (lbm_set_staging): tensor maps of both population sets, status word
-    int staged = 0;                       // 0 off, 1 persistent double-buffered, 2 one tile per block
+    bool staged = false;
     lbm::StageMaps stage_maps[2];
     int* stage_status = nullptr;
-    int sms = 0;
     // y slab (lbm_slab_create): ghost rows below / above the band, first global row
     bool slab = false;
     int slab_ghost[2] = {0, 0};

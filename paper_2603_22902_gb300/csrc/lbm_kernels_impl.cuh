@@ -61,27 +61,18 @@ cudaError_t launch_export(const KParams& P, const void* pin, const void* ain, do
 
 template <int N, class Pr>
 cudaError_t launch_staged(const KParams& P, const StageMaps& maps, const void* pin, void* pout, const void* ain,
-                          void* aout, int* status, int sms, int mode, cudaStream_t st)
+                          void* aout, int* status, cudaStream_t st)
 {
     if constexpr (staged_policy<Pr>() && N == 2) {
         using Lay = StageLayout<N, Pr>;
         using TA = typename Pr::TA;
         const int tiles_x = (P.nx + STAGE_TX - 1) / STAGE_TX, tiles_y = (P.ny + STAGE_TY - 1) / STAGE_TY;
-        if (mode == 2) {
-            cudaError_t e = cudaFuncSetAttribute(staged_tile_kernel<N, Pr>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::TOTAL1);
-            if (e != cudaSuccess) return e;
-            staged_tile_kernel<N, Pr><<<dim3(tiles_x, tiles_y), STAGE_NT, Lay::TOTAL1, st>>>(
-                P, maps, pin, pout, (const TA*)ain, (TA*)aout, status);
-            return cudaGetLastError();
-        }
-        cudaError_t e = cudaFuncSetAttribute(staged_step_kernel<N, Pr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(staged_tile_kernel<N, Pr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              Lay::TOTAL);
         if (e != cudaSuccess) return e;
-        const int ntiles = tiles_x * tiles_y;
-        const int grid = std::min(ntiles, 2 * sms);
-        staged_step_kernel<N, Pr><<<grid, STAGE_NT, Lay::TOTAL, st>>>(P, maps, pin, pout, (const TA*)ain, (TA*)aout,
-                                                                      tiles_x, ntiles, status);
+        staged_tile_kernel<N, Pr><<<dim3(tiles_x, tiles_y), STAGE_NT, Lay::TOTAL, st>>>(P, maps, pin, pout,
+                                                                                         (const TA*)ain, (TA*)aout,
+                                                                                         status);
         return cudaGetLastError();
     } else {
         return cudaErrorNotSupported;
@@ -213,7 +204,7 @@ cudaError_t launch_adj_init(const KParams& P, const double* phi0, const double* 
     template cudaError_t launch_step<N, PR>(const KParams&, const void*, void*, const void*, void*, int,           \
                                             cudaStream_t);                                                          \
     template cudaError_t launch_staged<N, PR>(const KParams&, const StageMaps&, const void*, void*, const void*,   \
-                                              void*, int*, int, int, cudaStream_t);                                 \
+                                              void*, int*, cudaStream_t);                                           \
     template cudaError_t launch_export<N, PR>(const KParams&, const void*, const void*, double*, double*, double*, \
                                               double*, double*, double*, double*, cudaStream_t);                    \
     template cudaError_t launch_init<N, PR>(const KParams&, const double*, const double*, const double*,           \

@@ -35,15 +35,14 @@ template <int N, class Pr>
 cudaError_t launch_init(const KParams& P, const double* phi, const double* T, const double* ux, const double* uy,
                         void* pop, void* aux, cudaStream_t st);
 // The step with its inputs staged by the TMA (lbm_staged.cuh): policies with 16-bit moving
-// populations, N = 2.  maps are the six tensor maps of the input set; status receives 1
-// when an mbarrier wait gave up.  cudaErrorNotSupported for other policies.
+// populations, N = 2, one block per tile.  maps are the six tensor maps of the input set;
+// status receives 1 when an mbarrier wait gave up.  cudaErrorNotSupported for other policies.
 struct StageMaps {
     CUtensorMap m[6];   // boxes A..F of lbm_staged.cuh
 };
-// mode 1: persistent grid, double-buffered stages; mode 2: one tile per block.
 template <int N, class Pr>
 cudaError_t launch_staged(const KParams& P, const StageMaps& maps, const void* pin, void* pout, const void* ain,
-                          void* aout, int* status, int sms, int mode, cudaStream_t st);
+                          void* aout, int* status, cudaStream_t st);
 template <class Pr>
 constexpr bool staged_policy()
 {

@@ -1,28 +1,28 @@
 // lbm_staged.cuh -- the fused step with its inputs staged in shared memory by the
 // tensor-memory accelerator (TMA), for the 16-bit storage policies.
 //
-// The one-cell step (lbm_step.cuh) is bound by the latency of its global loads: every
-// block loads its tile's and ring's populations, waits, computes, loads the flow
-// populations, waits again.  Here a persistent grid of two blocks per SM walks the tiles
-// of the lattice; while a block computes one interior 32 x 8 tile from shared memory, the
-// TMA copies the next tile's inputs into the other half of a double buffer, so the copy
-// of tile k + 1 overlaps the arithmetic of tile k.  Six tensor copies per tile, issued by
-// one thread and completing on one mbarrier:
+// In the one-cell step (lbm_step.cuh) every thread loads its cell's populations and
+// lagged values, and the ring cells' phase-field and enthalpy populations, with ~40
+// scalar global loads and their address arithmetic, waits, computes, then loads the flow
+// populations and waits again.  Here thread 0 of a block copies everything the tile needs
+// with six tensor copies that complete on one mbarrier:
 //   A  the eight moving planes of f, own cells          [8][8][32]
 //   B  the moving planes of g_p and h, tile and ring     [8(N+1)][10][32 + 2 pad]
 //   C  the rest plane of f, own cells                    [1][8][32]
 //   D  the rest planes of g_p and h, tile and ring        [N+1][10][32 + 2 pad]
 //   E  the lagged mdot' and Q', tile and ring             [2][10][32 + 2 pad]
 //   F  the other lagged planes, own cells                 [1 + 2N][8][32]
-// A box that includes the ring starts pad = 16 / element-size cells left of the tile, so
-// its first x coordinate is on a 16-byte boundary (the tile's x0 is a multiple of 32),
-// and is 16-byte multiples wide; its rows y0 - 1 .. y0 + 8 lie inside the lattice for an
-// interior tile, and columns beyond the right side are filled with zeros and never read.
-// The arithmetic is step_tile_l of the one-cell step with a loader that reads the staged
-// copy, so every interior cell is computed exactly as the one-cell step computes it; tiles
-// that touch a side of the lattice run the one-cell step itself from global memory.
-// Every wait on an mbarrier is bounded: a wait that gives up sets a status word (reported
-// as LBM_ETIMEOUT), waits (bounded) for the block's own copies in flight and leaves.
+// and the tile is computed from shared memory: one memory latency per block instead of
+// two, and shared-memory reads instead of global loads.  A box that includes the ring
+// starts pad = 16 / element-size cells left of the tile, so its first x coordinate is on a
+// 16-byte boundary (the tile's x0 is a multiple of 32), and is a multiple of 16 bytes
+// wide; its rows y0 - 1 .. y0 + 8 lie inside the lattice for an interior tile, and columns
+// beyond the right side are filled with zeros and never read.  The arithmetic is
+// step_tile_l of the one-cell step with a loader that reads the staged copy, so every cell
+// is computed exactly as the one-cell step computes it (the two forms agree bit for bit);
+// tiles that touch a side of the lattice run the one-cell step itself.  Every wait on the
+// mbarrier is bounded: a wait that gives up sets a status word (reported as
+// LBM_ETIMEOUT), waits (bounded) for the copies in flight and leaves.
 #pragma once
 
 #include "lbm_launch.cuh"
@@ -51,12 +51,10 @@ struct StageLayout {
     static constexpr int OA = 0, OB = OA + stage_round(A), OC = OB + stage_round(B), OD = OC + stage_round(C),
                          OE = OD + stage_round(D), OF = OE + stage_round(E), BYTES = OF + stage_round(F);
     static constexpr int TX_BYTES = A + B + C + D + E + F;   // what the six copies deliver
-    // dynamic shared memory of a block: two stages, two mbarriers, the one-cell step's tile
-    static constexpr int SMEM_ONE = tile_smem_elems<N, STAGE_TX, STAGE_TY, Pr>() * (int)sizeof(typename Pr::R);
+    // dynamic shared memory of a block: the stage, the mbarrier, the one-cell step's tile
     // (TOTAL has 128 bytes of slack: the kernel aligns its base to 128 bytes)
-    static constexpr int OBAR = 2 * BYTES, OONE = OBAR + 128, TOTAL = OONE + stage_round(SMEM_ONE) + 128;
-    // one stage (one tile per block)
-    static constexpr int OBAR1 = BYTES, OONE1 = OBAR1 + 128, TOTAL1 = OONE1 + stage_round(SMEM_ONE) + 128;
+    static constexpr int SMEM_ONE = tile_smem_elems<N, STAGE_TX, STAGE_TY, Pr>() * (int)sizeof(typename Pr::R);
+    static constexpr int OBAR = BYTES, OONE = OBAR + 128, TOTAL = OONE + stage_round(SMEM_ONE) + 128;
 };
 
 // Reads of one staged interior tile; a cell is (lx, ly) of the tile with its ring.
@@ -152,8 +150,6 @@ __device__ __forceinline__ void stage_issue(const StageMaps& M, unsigned char* s
 {
     using Lay = StageLayout<N, Pr>;
     const int x0 = bx * STAGE_TX, y0 = by * STAGE_TY;
-    // the previous readers of this stage (generic proxy) are ordered before the copies
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect(bar, (unsigned)Lay::TX_BYTES);
     const unsigned s = smem_addr(stage);
     tma_load_3d(s + Lay::OA, &M.m[0], x0, y0, 0, bar);
@@ -164,67 +160,10 @@ __device__ __forceinline__ void stage_issue(const StageMaps& M, unsigned char* s
     tma_load_3d(s + Lay::OF, &M.m[5], x0, y0, 2, bar);
 }
 
-// One step over all tiles of the lattice: a persistent grid, tiles in order t = blockIdx.x,
-// blockIdx.x + gridDim.x, ...; interior tiles from a double-buffered staged copy, the
-// others by the one-cell step.
-template <int N, class Pr>
-__global__ void __launch_bounds__(STAGE_NT, 2)
-staged_step_kernel(const KParams P, const __grid_constant__ StageMaps M, const void* __restrict__ pin_base,
-                   void* __restrict__ pout_base, const typename Pr::TA* __restrict__ ain,
-                   typename Pr::TA* __restrict__ aout, int tiles_x, int ntiles, int* __restrict__ status)
-{
-    using Lay = StageLayout<N, Pr>;
-    using R = typename Pr::R;
-    extern __shared__ __align__(128) unsigned char dyn_raw[];
-    // tensor copies land on 128-byte boundaries of shared memory
-    unsigned char* dyn = dyn_raw + ((128u - (smem_addr(dyn_raw) & 127u)) & 127u);
-    unsigned char* stage[2] = {dyn, dyn + Lay::BYTES};
-    const unsigned bar[2] = {smem_addr(dyn + Lay::OBAR), smem_addr(dyn + Lay::OBAR + 8)};
-    R* one = reinterpret_cast<R*>(dyn + Lay::OONE);
-    const int tid = threadIdx.x;
-
-    if (tid == 0) {
-        mbar_init(bar[0], 1);
-        mbar_init(bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    const int first = blockIdx.x;
-    if (tid == 0 && first < ntiles && stage_interior(P, first % tiles_x, first / tiles_x))
-        stage_issue<N, Pr>(M, stage[0], bar[0], first % tiles_x, first / tiles_x);
-    unsigned phase = 0;   // bit b: parity of the next completion of stage b
-    int k = 0;
-    for (int t = first; t < ntiles; t += gridDim.x, ++k) {
-        const int b = k & 1;
-        const int bx = t % tiles_x, by = t / tiles_x;
-        const int nxt = t + gridDim.x;
-        const bool nxt_staged = nxt < ntiles && stage_interior(P, nxt % tiles_x, nxt / tiles_x);
-        if (tid == 0 && nxt_staged) stage_issue<N, Pr>(M, stage[b ^ 1], bar[b ^ 1], nxt % tiles_x, nxt / tiles_x);
-        if (stage_interior(P, bx, by)) {
-            const bool ok = mbar_wait(bar[b], (phase >> b) & 1u);
-            phase ^= 1u << b;
-            if (!__syncthreads_and(ok)) {
-                // give up: report, let the copy still in flight land, leave
-                if (tid == 0) {
-                    atomicExch(status, 1);
-                    if (nxt_staged) mbar_wait(bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
-                }
-                __syncthreads();
-                return;
-            }
-            const StagedLoader<N, Pr> ld{P, stage[b]};
-            step_tile_l<N, STAGE_TX, STAGE_TY, true, Pr>(P, ld, pout_base, aout, ExportPtrs{}, bx, by, one);
-        } else {
-            step_tile<N, STAGE_TX, STAGE_TY, true, Pr>(P, pin_base, pout_base, ain, aout, ExportPtrs{}, bx, by, one);
-        }
-        __syncthreads();   // stage b and the one-cell tile free for reuse
-    }
-}
-
-// The same staging with one tile per block (a grid of all tiles, up to four blocks per SM):
-// thread 0 issues the tile's six copies, every thread waits for them, and the tile is
-// computed from the staged copy; tiles that touch a side run the one-cell step.
+// One step: one block per tile (a grid of all tiles, up to four blocks per SM).  In an
+// interior tile thread 0 issues the tile's six copies, every thread waits for them, and
+// the tile is computed from the staged copy; tiles that touch a side run the one-cell
+// step from global memory.
 template <int N, class Pr>
 __global__ void __launch_bounds__(STAGE_NT, 4)
 staged_tile_kernel(const KParams P, const __grid_constant__ StageMaps M, const void* __restrict__ pin_base,
@@ -235,13 +174,13 @@ staged_tile_kernel(const KParams P, const __grid_constant__ StageMaps M, const v
     using R = typename Pr::R;
     extern __shared__ __align__(128) unsigned char dyn_raw[];
     unsigned char* dyn = dyn_raw + ((128u - (smem_addr(dyn_raw) & 127u)) & 127u);
-    R* one = reinterpret_cast<R*>(dyn + Lay::OONE1);
+    R* one = reinterpret_cast<R*>(dyn + Lay::OONE);
     const int bx = blockIdx.x, by = blockIdx.y;
     if (!stage_interior(P, bx, by)) {
         step_tile<N, STAGE_TX, STAGE_TY, true, Pr>(P, pin_base, pout_base, ain, aout, ExportPtrs{}, bx, by, one);
         return;
     }
-    const unsigned bar = smem_addr(dyn + Lay::OBAR1);
+    const unsigned bar = smem_addr(dyn + Lay::OBAR);
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

@@ -366,7 +366,7 @@ def make_structs(case, precision="fp64", diag_every=0):
 class Solver:
     """One solver handle on the current CUDA device, fed from a ``workloads.Case``."""
 
-    def __init__(self, case, precision="fp64", diag_every=0, tile=None, stream=None, staged=False):
+    def __init__(self, case, precision="fp64", diag_every=0, tile=None, stream=None, staged=None):
         import torch
         self.torch = torch
         self.case = case
@@ -378,8 +378,8 @@ class Solver:
         lbm_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream))
         if tile is not None:
             lbm_set_tile(self.h, *tile)
-        if staged:
-            lbm_set_staging(self.h, int(staged))
+        if staged is not None:   # None: the library's default (staged where it applies)
+            lbm_set_staging(self.h, 1 if staged else 0)
 
     def set_fields(self, phi=None, T=None, ux=None, uy=None):
         """Initial state from device tensors (default: the case's own fields)."""
