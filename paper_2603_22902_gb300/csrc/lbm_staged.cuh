@@ -66,6 +66,7 @@ struct StagedLoader {
     using TA = typename Pr::TA;
     using Lay = StageLayout<N, Pr>;
     using Cell = int;   // ly * 64 + lx
+    static constexpr bool GLOBAL = false;
     const KParams& P;
     const unsigned char* st;   // the stage
     __device__ __forceinline__ bool locate(int lx, int ly, Cell& cell) const

@@ -132,37 +132,20 @@ __device__ __forceinline__ void st_pop(const KParams& P, const PopView<Pr>& v, i
 // Where a step reads its inputs.  A loader addresses a cell of the tile-with-ring by a
 // Cell value and gives its populations (dequantised) and lagged values.
 //   GlobalLoader: the population and lagged sets in global memory, cells by their index in
-//     the lattice.  locate(lx, ly) maps a position of the tile-with-ring to a cell: periodic
-//     sides wrap (a full modulo, since a tile may be wider or taller than the lattice);
-//     other sides clamp, and the position is reported as beyond the lattice, to be filled
-//     by the ghost rule.  No address outside the planes is ever formed.
+//     the lattice (step_tile_l maps a position of the tile-with-ring to it).
 //   StagedLoader: the same inputs of one interior tile copied into shared memory by the
 //     tensor-memory accelerator (lbm_staged.cuh); cells by their position in the tile.
 template <class Pr>
 struct GlobalLoader {
     using R = typename Pr::R;
     using Cell = long long;
+    static constexpr bool GLOBAL = true;   // step_tile_l locates the cells itself
     const KParams& P;
     PopView<Pr> pin;
     const typename Pr::TA* __restrict__ ain;
-    int x0, y0;        // lattice position of the tile's first cell
-    bool xper, yper;
-    __device__ __forceinline__ bool locate(int lx, int ly, Cell& cell) const
-    {
-        int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        bool beyond = false;
-        if (gx < 0 || gx >= P.nx) {
-            if (xper) gx = wrap_index(gx, P.nx);
-            else { beyond = true; gx = min(max(gx, 0), P.nx - 1); }
-        }
-        if (gy < 0 || gy >= P.ny) {
-            if (yper) gy = wrap_index(gy, P.ny);
-            else { beyond = true; gy = min(max(gy, 0), P.ny - 1); }
-        }
-        cell = (long long)gy * P.nx + gx;
-        return !beyond;
-    }
-    __device__ __forceinline__ Cell own(int x, int y, int, int) const { return (long long)y * P.nx + x; }
+    long long S;
+    int nx;
+    __device__ __forceinline__ Cell own(int x, int y, int, int) const { return (long long)y * nx + x; }
     template <int KIND>
     __device__ __forceinline__ R pop(int s, int i, Cell c, int site) const
     {
@@ -175,7 +158,7 @@ struct GlobalLoader {
     }
     __device__ __forceinline__ R aux(int a, Cell c, int site) const
     {
-        return (R)LBM_LDX(Pr::COH, P, ain, a * P.S + c, P.aux_elems, site);
+        return (R)LBM_LDX(Pr::COH, P, ain, a * S + c, P.aux_elems, site);
     }
 };
 
@@ -292,7 +275,7 @@ __device__ __forceinline__ void halo_moments(const KParams& P, const PopView<Pr>
                                              const typename Pr::TA* __restrict__ ain, long long c,
                                              typename Pr::R (&phi)[N], typename Pr::R& rho, typename Pr::R& psi)
 {
-    const GlobalLoader<Pr> ld{P, pin, ain, 0, 0, false, false};
+    const GlobalLoader<Pr> ld{P, pin, ain, P.S, P.nx};
     halo_moments_l<N, Pr>(P, ld, c, phi, rho, psi);
 }
 
@@ -465,10 +448,29 @@ __device__ __forceinline__ void step_tile_l(const KParams& P, const L& ld, void*
     const Coef<R>& C = coef<R>(P);
     using Cell = typename L::Cell;
 
-    // Position (lx, ly) of the tile-with-ring as a cell of the loader (GlobalLoader: brought
-    // into range before anything else, so no address outside the planes is ever formed; a
-    // position beyond a non-periodic side is reported, to be filled by the ghost rule).
-    auto locate = [&](int lx, int ly, Cell& cell) { return ld.locate(lx, ly, cell); };
+    // Position (lx, ly) of the tile-with-ring as a cell of the loader.  In global memory the
+    // coordinates are brought into range before anything else (periodic: full modulo, since
+    // a tile may be wider / taller than the domain; otherwise clamped, and the position is
+    // reported as beyond the domain, to be filled by the ghost rule), so no address outside
+    // the planes is ever formed; a staged tile has its ring inside the lattice.
+    auto locate = [&](int lx, int ly, Cell& cell) {
+        if constexpr (L::GLOBAL) {
+            int gx = x0 + lx - 1, gy = y0 + ly - 1;
+            bool beyond = false;
+            if (gx < 0 || gx >= nx) {
+                if (xper) gx = wrap_index(gx, nx);
+                else { beyond = true; gx = min(max(gx, 0), nx - 1); }
+            }
+            if (gy < 0 || gy >= ny) {
+                if (yper) gy = wrap_index(gy, ny);
+                else { beyond = true; gy = min(max(gy, 0), ny - 1); }
+            }
+            cell = (long long)gy * nx + gx;
+            return !beyond;
+        } else {
+            return ld.locate(lx, ly, cell);
+        }
+    };
     R phi[N], rhoH, fl, T, rho, psi, mu, lam, cp, chi;
     if constexpr (Pr::COMPACT) {
         // ---- stages A + B: one code path for all (TX + 2)(TY + 2) positions, so that
@@ -824,8 +826,7 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
                                           typename Pr::TA* __restrict__ aout, const ExportPtrs& ex, int bx, int by,
                                           typename Pr::R* smem)
 {
-    const GlobalLoader<Pr> ld{P, pop_view<Pr>(P, pin_base), ain, bx * TX, by * TY, P.bc[0] == PERIODIC,
-                              P.bc[2] == PERIODIC};
+    const GlobalLoader<Pr> ld{P, pop_view<Pr>(P, pin_base), ain, P.S, P.nx};
     step_tile_l<N, TX, TY, COLLIDE, Pr>(P, ld, pout_base, aout, ex, bx, by, smem);
 }
 
