@@ -68,11 +68,12 @@ ISSUE_PEAK_GWINST = 152 * 4 * 2.070
 # A changed kernel has another digest, and then these counts are not reported.
 # (DRAM bytes are what ncu saw during the launch: part of the writes of a launch is
 # still in L2 when it ends and reaches DRAM during the next one.)
-_D = "d38540d008cb7d235e911051458fc37dbb6b5db0c23210af5acc86e62315394e"
+_D = "e62d4d26ff8cf5e2dc31a0cd5c3fa2c7ec9767588d33cfc1db9933a63ec844f2"
 NCU_COUNTS = {
-    ("fp64", 2): {"digest": _D, "fp64_inst": 487.0, "fp64_flop": 660.8, "warp_inst": 102.4, "dram_bytes": 518.7},
-    ("df64", 2): {"digest": _D, "fp64_inst": 0.08, "warp_inst": 176.0, "fp32_inst": 4089.1, "dram_bytes": 648.6},
-    ("fp16s", 2): {"digest": _D, "fp64_inst": 0.06, "fp64_flop": 0.04, "warp_inst": 50.8, "dram_bytes": 108.5},
+    ("fp64", 2): {"digest": _D, "fp64_inst": 487.0, "fp64_flop": 660.8, "warp_inst": 102.4, "dram_bytes": 520.0},
+    ("df64", 2): {"digest": _D, "fp64_inst": 0.08, "warp_inst": 176.8, "fp32_inst": 4089.1, "dram_bytes": 645.6},
+    # the FP16-storage step is the TMA-staged kernel (staged_tile_kernel) where it applies
+    ("fp16s", 2): {"digest": _D, "fp64_inst": 0.06, "fp64_flop": 0.04, "warp_inst": 44.0, "dram_bytes": 108.6},
 }
 
 
@@ -426,10 +427,11 @@ def run_gpu(args):
     return 0
 
 
-def timed_mlups(lbm, case, precision, steps, stream, flush):
-    """Same protocol as the headline: L2 flushed before every timed step, CUDA events."""
+def timed_mlups(lbm, case, precision, steps, stream, flush, staged=None):
+    """Same protocol as the headline: L2 flushed before every timed step, CUDA events.
+    staged: None for the library's default form, else force the TMA-staged form on / off."""
     import torch
-    s = lbm.Solver(case, precision=precision).set_fields()
+    s = lbm.Solver(case, precision=precision, staged=staged).set_fields()
     s.step(5)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -494,6 +496,8 @@ def extra_workloads(args, lbm, stream, flush):
     """The other single-GPU configurations, timed by this same run:
     - compound_drop_1024: 1024 x 1024, N = 3, each policy timed like the headline (L2
       flushed before every timed step, CUDA events per step);
+    - staged_fp16s: the FP16-storage step of the 512^2 and 1024^2 sessile drops in its
+      TMA-staged form and in the one-launch form, timed the same way;
     - batch_sweep_256: the 256-drop sweep in one batch (FP16 storage), autotuned plan,
       CUDA events per call of --batch-chunk steps (state far larger than L2);
     - adjoint_impurity_512: one call of the hand-written adjoint on the 512 x 512 pool with
@@ -515,6 +519,16 @@ def extra_workloads(args, lbm, stream, flush):
             r[prec] = {"value": round(mlups, 2), "unit": "MLUPS", "bytes_per_lu": bpl,
                        "hbm_frac": round(bpl * mlups * 1e6 / 1e9 / hbm_peak, 4)}
         out["compound_drop_1024"] = r
+    if "staged" in parts:
+        # the FP16-storage step with its inputs staged by tensor copies against the one-launch form
+        r = {}
+        for n, R in ((512, 100.0), (1024, 200.0)):
+            case = W.sessile_drop(n=n, R=R)
+            a = timed_mlups(lbm, case, "fp16s", 200, stream, flush, staged=False)
+            b = timed_mlups(lbm, case, "fp16s", 200, stream, flush, staged=True)
+            r[case.name] = {"one_launch": round(a, 2), "staged": round(b, 2), "unit": "MLUPS",
+                            "hbm_frac_staged": round(bytes_per_lu(2, "fp16s") * b * 1e6 / 1e9 / hbm_peak, 4)}
+        out["staged_fp16s"] = r
     if "batch" in parts:
         out["batch_sweep_256"] = batch_measure(args, lbm, stream, steps=200, warmup=20)
     if "adjoint" in parts:
@@ -714,7 +728,7 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="compound,batch,adjoint",
+    ap.add_argument("--extras", default="compound,staged,batch,adjoint",
                     help="other configurations timed beside the headline ('none' to skip)")
     ap.add_argument("--clocks-dir", default=None, help="directory for the raw nvidia-smi clock samples")
     args = ap.parse_args(argv)
