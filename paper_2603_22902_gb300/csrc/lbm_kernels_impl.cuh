@@ -18,8 +18,8 @@ static cudaError_t launch_fused_t(const KParams& P, const void* pin, void* pout,
                                   ExportPtrs ex, cudaStream_t st)
 {
     using TA = typename Pr::TA;
-    dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-    fused_step_kernel<N, TX, TY, COLLIDE, Pr><<<grid, TX * TY, 0, st>>>(P, pin, pout, (const TA*)ain, (TA*)aout, ex);
+    const int tiles = ((P.nx + TX - 1) / TX) * ((P.ny + TY - 1) / TY);
+    fused_step_kernel<N, TX, TY, COLLIDE, Pr><<<tiles, TX * TY, 0, st>>>(P, pin, pout, (const TA*)ain, (TA*)aout, ex);
     return cudaGetLastError();
 }
 
@@ -70,9 +70,9 @@ cudaError_t launch_staged(const KParams& P, const StageMaps& maps, const void* p
         cudaError_t e = cudaFuncSetAttribute(staged_tile_kernel<N, Pr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              Lay::TOTAL);
         if (e != cudaSuccess) return e;
-        staged_tile_kernel<N, Pr><<<dim3(tiles_x, tiles_y), STAGE_NT, Lay::TOTAL, st>>>(P, maps, pin, pout,
-                                                                                         (const TA*)ain, (TA*)aout,
-                                                                                         status);
+        staged_tile_kernel<N, Pr><<<tiles_x * tiles_y, STAGE_NT, Lay::TOTAL, st>>>(P, maps, pin, pout,
+                                                                                    (const TA*)ain, (TA*)aout,
+                                                                                    status);
         return cudaGetLastError();
     } else {
         return cudaErrorNotSupported;

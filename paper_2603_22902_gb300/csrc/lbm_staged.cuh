@@ -16,13 +16,17 @@
 // two, and shared-memory reads instead of global loads.  A box that includes the ring
 // starts pad = 16 / element-size cells left of the tile, so its first x coordinate is on a
 // 16-byte boundary (the tile's x0 is a multiple of 32), and is a multiple of 16 bytes
-// wide; its rows y0 - 1 .. y0 + 8 lie inside the lattice for an interior tile, and columns
-// beyond the right side are filled with zeros and never read.  The arithmetic is
-// step_tile_l of the one-cell step with a loader that reads the staged copy, so every cell
-// is computed exactly as the one-cell step computes it (the two forms agree bit for bit);
-// tiles that touch a side of the lattice run the one-cell step itself.  Every wait on the
-// mbarrier is bounded: a wait that gives up sets a status word (reported as
-// LBM_ETIMEOUT), waits (bounded) for the copies in flight and leaves.
+// wide.  Every tile is staged this way: positions of a box beyond the lattice (left of
+// x = 0, below y = 0, past the right or top side) are filled with zeros by the copy and
+// are either never read (beyond a wall or an outflow side: the ghost rule replaces them)
+// or, across a periodic side, read again from the cells they wrap to (stage_wrap).  The
+// arithmetic is step_tile_l of the one-cell step with a loader that reads the stage, so
+// every cell is computed exactly as the one-cell step computes it (the two forms agree
+// bit for bit), and that code exists once in the kernel (a second copy for the tiles at
+// the sides, reading global memory, overflowed the instruction cache).  The tiles at the
+// sides run first (ring_first_tile).  Every wait on the mbarrier is bounded: a wait that
+// gives up sets a status word (reported as LBM_ETIMEOUT), waits (bounded) for the copies
+// in flight and leaves.
 #pragma once
 
 #include "lbm_launch.cuh"
@@ -57,7 +61,7 @@ struct StageLayout {
     static constexpr int OBAR = BYTES, OONE = OBAR + 128, TOTAL = OONE + stage_round(SMEM_ONE) + 128;
 };
 
-// Reads of one staged interior tile; a cell is (lx, ly) of the tile with its ring.
+// Reads of one staged tile; a cell is (lx, ly) of the tile with its ring.
 template <int N, class Pr>
 struct StagedLoader {
     using R = typename Pr::R;
@@ -69,10 +73,18 @@ struct StagedLoader {
     static constexpr bool GLOBAL = false;
     const KParams& P;
     const unsigned char* st;   // the stage
+    int x0, y0;                // the tile's first cell
+    bool edge;                 // the ring reaches a side of the lattice
+    // A position beyond a side that is not periodic is no cell (the ghost rule fills it);
+    // every other position, across a periodic side too, was staged as a cell.
     __device__ __forceinline__ bool locate(int lx, int ly, Cell& cell) const
     {
         cell = ly * 64 + lx;
-        return true;
+        if (!edge) return true;
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        const bool bx = P.bc[0] != PERIODIC && (gx < 0 || gx >= P.nx);
+        const bool by = P.bc[2] != PERIODIC && (gy < 0 || gy >= P.ny);
+        return !(bx || by);
     }
     __device__ __forceinline__ Cell own(int, int, int tx, int ty) const { return (ty + 1) * 64 + tx + 1; }
     template <int KIND>
@@ -137,12 +149,11 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
         : "memory");
 }
 
-// An interior tile for staging: its ring lies inside the lattice (no wrap, no boundary
-// rule), and its x0 leaves room for the left pad of the boxes.
-__device__ __forceinline__ bool stage_interior(const KParams& P, int bx, int by)
+// The tile's one-cell ring lies inside the lattice: no position of the tile with its
+// ring is beyond a side or across a periodic one.
+__device__ __forceinline__ bool ring_inside(const KParams& P, int x0, int y0)
 {
-    const int x0 = bx * STAGE_TX, y0 = by * STAGE_TY;
-    return x0 >= STAGE_TX && x0 + STAGE_TX <= P.nx - 1 && y0 >= 1 && y0 + STAGE_TY <= P.ny - 1;
+    return x0 >= 1 && x0 + STAGE_TX <= P.nx - 1 && y0 >= 1 && y0 + STAGE_TY <= P.ny - 1;
 }
 
 // Thread 0: the six copies of tile (bx, by) into `stage`, completing on `bar`.
@@ -161,10 +172,69 @@ __device__ __forceinline__ void stage_issue(const StageMaps& M, unsigned char* s
     tma_load_3d(s + Lay::OF, &M.m[5], x0, y0, 2, bar);
 }
 
-// One step: one block per tile (a grid of all tiles, up to four blocks per SM).  In an
-// interior tile thread 0 issues the tile's six copies, every thread waits for them, and
-// the tile is computed from the staged copy; tiles that touch a side run the one-cell
-// step from global memory.
+// Positions of the ring boxes (B, D, E) that lie across a periodic side: the tensor
+// copies fill them with zeros (the box starts left of or below the lattice, or runs past
+// its right or top side), so they are read again, with plain loads, from the cells they
+// wrap to.  Positions beyond a side that is not periodic keep the zeros (the ghost rule
+// replaces them); the own-cell boxes (A, C, F) are read only at cells of the lattice.
+// The work is one load per (position, plane): the wrapped columns (10 positions each)
+// and rows (34 each) of the tile with its ring times the 8 (N + 1) + (N + 1) + 2 planes,
+// spread over the block (a corner in both lists is read twice, to the same value).
+template <int N, class Pr>
+__device__ __forceinline__ void stage_wrap(const KParams& P, const void* __restrict__ pin_base,
+                                           const typename Pr::TA* __restrict__ ain, unsigned char* st, int x0, int y0)
+{
+    using Lay = StageLayout<N, Pr>;
+    using TR = typename Pr::TR;
+    using TM = typename Pr::TM;
+    using TA = typename Pr::TA;
+    const PopView<Pr> v = pop_view<Pr>(P, pin_base);
+    const int nx = P.nx, ny = P.ny;
+    const long long S = P.S;
+    const bool xper = P.bc[0] == PERIODIC, yper = P.bc[2] == PERIODIC;
+    constexpr int RW = STAGE_TX + 2, PLANES = 9 * (N + 1) + 2;
+    // wrapped columns: lx = 0 (x0 = 0) and lx = cR .. RW - 1 (past the right side);
+    // wrapped rows: ly = 0 (y0 = 0) and ly = rT .. H - 1 (past the top side)
+    const int nL = xper && x0 == 0 ? 1 : 0, cR = nx - x0 + 1, nR = xper && cR < RW ? RW - cR : 0;
+    const int nB = yper && y0 == 0 ? 1 : 0, rT = ny - y0 + 1, nT = yper && rT < Lay::H ? Lay::H - rT : 0;
+    const int ncol = (nL + nR) * Lay::H, items = (ncol + (nB + nT) * RW) * PLANES;
+    TM* B = reinterpret_cast<TM*>(st + Lay::OB);
+    TR* D = reinterpret_cast<TR*>(st + Lay::OD);
+    TA* E = reinterpret_cast<TA*>(st + Lay::OE);
+    for (int e = threadIdx.x; e < items; e += STAGE_NT) {
+        const int pl = e % PLANES, pos = e / PLANES;
+        int lx, ly;
+        if (pos < ncol) {
+            const int k = pos / Lay::H;
+            ly = pos % Lay::H;
+            lx = k < nL ? 0 : cR + (k - nL);
+        } else {
+            const int k = (pos - ncol) / RW;
+            lx = (pos - ncol) % RW;
+            ly = k < nB ? 0 : rT + (k - nB);
+        }
+        int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        const bool xout = gx < 0 || gx >= nx, yout = gy < 0 || gy >= ny;
+        if ((xout && !xper) || (yout && !yper)) continue;   // beyond a wall or an outflow side
+        if (xout) gx = wrap_index(gx, nx);
+        if (yout) gy = wrap_index(gy, ny);
+        const long long c = (long long)gy * nx + gx;
+        if (pl < 8 * (N + 1))
+            B[(pl * Lay::H + ly) * Lay::WM + lx - 1 + Lay::PM] = LBM_LD(P, v.move, (8 + pl) * S + c, P.move_elems, 43);
+        else if (pl < 9 * (N + 1))
+            D[((pl - 8 * (N + 1)) * Lay::H + ly) * Lay::WR + lx - 1 + Lay::PR] =
+                LBM_LD(P, v.rest, (1 + pl - 8 * (N + 1)) * S + c, P.rest_elems, 44);
+        else
+            E[((pl - 9 * (N + 1)) * Lay::H + ly) * Lay::WA + lx - 1 + Lay::PA] =
+                LBM_LD(P, ain, (pl - 9 * (N + 1)) * S + c, P.aux_elems, 45);
+    }
+}
+
+// One step: one block per tile (a one-dimensional grid of all tiles, up to four blocks
+// per SM, the tiles at the sides first).  Every tile is computed from its stage in shared
+// memory, so the step's arithmetic is compiled once: thread 0 issues the tile's six tensor
+// copies, every thread waits for them, and a tile at a periodic side then reads its
+// wrapped positions again (stage_wrap).
 template <int N, class Pr>
 __global__ void __launch_bounds__(STAGE_NT, 4)
 staged_tile_kernel(const KParams P, const __grid_constant__ StageMaps M, const void* __restrict__ pin_base,
@@ -176,11 +246,9 @@ staged_tile_kernel(const KParams P, const __grid_constant__ StageMaps M, const v
     extern __shared__ __align__(128) unsigned char dyn_raw[];
     unsigned char* dyn = dyn_raw + ((128u - (smem_addr(dyn_raw) & 127u)) & 127u);
     R* one = reinterpret_cast<R*>(dyn + Lay::OONE);
-    const int bx = blockIdx.x, by = blockIdx.y;
-    if (!stage_interior(P, bx, by)) {
-        step_tile<N, STAGE_TX, STAGE_TY, true, Pr>(P, pin_base, pout_base, ain, aout, ExportPtrs{}, bx, by, one);
-        return;
-    }
+    int bx, by;
+    ring_first_tile(blockIdx.x, (P.nx + STAGE_TX - 1) / STAGE_TX, (P.ny + STAGE_TY - 1) / STAGE_TY, bx, by);
+    const int x0 = bx * STAGE_TX, y0 = by * STAGE_TY;
     const unsigned bar = smem_addr(dyn + Lay::OBAR);
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
@@ -198,7 +266,14 @@ staged_tile_kernel(const KParams P, const __grid_constant__ StageMaps M, const v
         __syncthreads();
         return;
     }
-    const StagedLoader<N, Pr> ld{P, dyn};
+    const bool inside = ring_inside(P, x0, y0);
+    const bool wraps = (P.bc[0] == PERIODIC && (x0 == 0 || x0 + STAGE_TX >= P.nx)) ||
+                       (P.bc[2] == PERIODIC && (y0 == 0 || y0 + STAGE_TY >= P.ny));
+    if (wraps) {
+        stage_wrap<N, Pr>(P, pin_base, ain, dyn, x0, y0);
+        __syncthreads();
+    }
+    const StagedLoader<N, Pr> ld{P, dyn, x0, y0, !inside};
     step_tile_l<N, STAGE_TX, STAGE_TY, true, Pr>(P, ld, pout_base, aout, ExportPtrs{}, bx, by, one);
 }
 

@@ -830,14 +830,46 @@ __device__ __forceinline__ void step_tile(const KParams& P, const void* __restri
     step_tile_l<N, TX, TY, COLLIDE, Pr>(P, ld, pout_base, aout, ex, bx, by, smem);
 }
 
-// One launch = one time step of one lattice, one block per tile.
+// Tile (bx, by) of block b of a one-dimensional grid of tx * ty tiles.  The tiles on the
+// outer ring of the tile grid (those at a side of the lattice: ghost pass, pushes with
+// the boundary rules, wrapped reads; about twice the time of an interior tile) take the
+// lowest block indices, so that they start in the first wave and overlap the interior
+// tiles of later waves instead of finishing last.  Grids of fewer than three tiles along
+// an axis are taken in order.
+__device__ __forceinline__ void ring_first_tile(int b, int tx, int ty, int& bx, int& by)
+{
+    if (tx < 3 || ty < 3) {
+        bx = b % tx;
+        by = b / tx;
+        return;
+    }
+    if (b < 2 * tx) {                       // bottom row, then top row
+        bx = b % tx;
+        by = b < tx ? 0 : ty - 1;
+        return;
+    }
+    const int k = b - 2 * tx;
+    if (k < 2 * (ty - 2)) {                 // left and right columns
+        bx = (k & 1) ? tx - 1 : 0;
+        by = 1 + (k >> 1);
+        return;
+    }
+    const int m = k - 2 * (ty - 2);         // interior tiles, row by row
+    bx = 1 + m % (tx - 2);
+    by = 1 + m / (tx - 2);
+}
+
+// One launch = one time step of one lattice, one block per tile (a one-dimensional grid,
+// the tiles at the sides first).
 template <int N, int TX, int TY, bool COLLIDE, class Pr>
 __global__ void __launch_bounds__(TX * TY, (LBM_OCC(Pr) + TX * TY - 1) / (TX * TY))
 fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __restrict__ pout_base,
                   const typename Pr::TA* __restrict__ ain, typename Pr::TA* __restrict__ aout, ExportPtrs ex)
 {
     __shared__ typename Pr::R smem[tile_smem_elems<N, TX, TY, Pr>()];
-    step_tile<N, TX, TY, COLLIDE, Pr>(P, pin_base, pout_base, ain, aout, ex, blockIdx.x, blockIdx.y, smem);
+    int bx, by;
+    ring_first_tile(blockIdx.x, (P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, bx, by);
+    step_tile<N, TX, TY, COLLIDE, Pr>(P, pin_base, pout_base, ain, aout, ex, bx, by, smem);
 }
 
 }  // namespace lbm

@@ -1,8 +1,10 @@
 """The TMA-staged form of the step (lbm_set_staging; FP16 and BF16 storage, N = 2, on by
 default where it applies): each interior tile's inputs are copied into shared memory by
-six tensor copies and the tile is computed from there.  It runs the arithmetic of the
-one-launch form cell by cell, so the two forms must agree bit for bit, and the staged form
-holds the one-launch form's bounds against the CPU oracle."""
+six tensor copies, a tile at a side of the lattice fills the same layout with its own
+loads (wrapping across periodic sides), and the tile is computed from there.  It runs the
+arithmetic of the one-launch form cell by cell, so the two forms must agree bit for bit,
+and the staged form holds the one-launch form's bounds against the CPU oracle.  The cases
+cover periodic, wall and outflow sides and tiles cut by the lattice's edge."""
 import numpy as np
 import pytest
 
@@ -43,6 +45,7 @@ CASES = {
                                                 seed=1),
     "sessile_cap_160x64_walls": lambda: W.sessile_cap(160, 64, 18.0, theta=110.0, ste=0.3, T_wall=-1.5),
     "film_16x256": lambda: W.film(nx=16, ny=256),
+    "sessile_72x60_ragged": lambda: W.sessile_drop(n=72, R=20.0, ny=60, theta=80.0),
 }
 
 
