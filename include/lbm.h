@@ -355,14 +355,20 @@ typedef struct lbm_batch lbm_batch;
 #define LBM_BATCH_PERSISTENT 0 /* one cooperative launch per tile-shape group and call;
                                   grid barrier between steps */
 #define LBM_BATCH_PER_STEP 1   /* one launch per tile-shape group and step */
-/* Either form: the launches of a call are captured into a CUDA graph the first time a
+#define LBM_BATCH_STAGED 2     /* the per-step form, with every tile of a 32x8-tile group
+                                  computed from a TMA-staged copy of its inputs (the staged
+                                  step of lbm_set_staging) where the group allows it: policy
+                                  LBM_FP16S or LBM_BF16S, N = 2, every case's nx a multiple
+                                  of 8; other groups run the per-step form.  The results
+                                  equal the per-step form's bit for bit. */
+/* Every form: the launches of a call are captured into a CUDA graph the first time a
  * call of that length runs, and the graph is replayed by later calls of that length. */
 
 /* Size classes of a case, by cells nx * ny: <= 128^2, <= 256^2, <= 384^2, larger. */
 #define LBM_BATCH_CLASSES 4
 
 typedef struct {
-    int mode;                          /* LBM_BATCH_PERSISTENT or LBM_BATCH_PER_STEP */
+    int mode;                          /* LBM_BATCH_PERSISTENT, LBM_BATCH_PER_STEP or LBM_BATCH_STAGED */
     int blocks_per_sm;                 /* persistent grid: resident blocks per SM, 0 = all that fit */
     int tile[LBM_BATCH_CLASSES][2];    /* tile (bx, by) per size class: 32x8, 64x4 or 16x16 */
     int graph;                         /* out: 1 when the calls replay a CUDA graph */
@@ -403,14 +409,15 @@ int lbm_batch_step(lbm_batch* b, long nsteps);
  * batch's queued work first.  polls < 0 is LBM_EINVAL. */
 int lbm_batch_set_wait_limit(lbm_batch* b, long long polls);
 
-/* Wait for the batch's queued work. Returns LBM_OK, LBM_ETIMEOUT (a grid-barrier wait
- * gave up; the barrier is reset) or LBM_ECUDA. */
+/* Wait for the batch's queued work. Returns LBM_OK, LBM_ETIMEOUT (a grid-barrier wait of
+ * the persistent form, or a wait of the staged form for its tensor copies, gave up; the
+ * barrier is reset, the state undefined) or LBM_ECUDA. */
 int lbm_batch_sync(lbm_batch* b);
 
 /* Tune the plan on the current state and set the best one (also written to *best
  * when best is not NULL).
- * - Candidates: each launch mode; each tile shape per size class present; fewer
- *   resident blocks per SM.
+ * - Candidates: each launch mode (LBM_BATCH_STAGED where a group allows it); each tile
+ *   shape per size class present; fewer resident blocks per SM.
  * - Each candidate is timed over trial_steps steps (>= 1) with CUDA events, after one
  *   untimed call of the same length.
  * - The state of every case, and its step count, are restored afterwards.

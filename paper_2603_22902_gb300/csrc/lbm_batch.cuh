@@ -9,7 +9,11 @@
 //     the tile list and meet at a grid barrier after every step (the next step of a
 //     case reads what the neighbouring tiles wrote).  Loads bypass L1 (Coherent<Pr>),
 //     since the blocks read data that other blocks wrote during the same launch.
-//   * per step: one launch per step, one block per tile, read-only-path loads.
+//   * per step: one launch per step, one block per tile, read-only-path loads;
+//   * staged (16-bit storage, N = 2, 32x8 tiles): the per-step form with each tile
+//     computed from a TMA-staged copy of its inputs (staged_tile_issue / _finish,
+//     lbm_staged.cuh), through six tensor maps per case and set kept in global memory;
+//     the copies are in flight while the block loads the case's parameter block.
 //
 // Ping-pong: for case c, set pop[k] holds the state when k == parity, a device byte of
 // the group.  The persistent kernel flips it itself when it has run an odd number of
@@ -19,6 +23,7 @@
 #include "lbm_device.cuh"
 #include "lbm_launch.cuh"
 #include "lbm_prec.cuh"
+#include "lbm_staged.cuh"
 #include "lbm_step.cuh"
 
 namespace lbm {
@@ -120,6 +125,28 @@ batch_step_kernel(const BatchTable T, int s)
     const int local = t - C.first_tile;
     step_tile<N, TX, TY, true, Pr>(sP, C.pop[a], const_cast<void*>(C.pop[a ^ 1]), (const TA*)C.aux[a],
                                    (TA*)C.aux[a ^ 1], ExportPtrs{}, local % C.tiles_x, local / C.tiles_x, smem);
+}
+
+// Staged form: one block per tile of the flat list (32x8 tiles), step s of the call;
+// maps[2 c + k] are the tensor maps of case c's population and lagged set k.
+template <int N, class Pr>
+__global__ void __launch_bounds__(STAGE_NT, 4)
+batch_staged_kernel(const BatchTable T, const StageMaps* __restrict__ maps, int s)
+{
+    extern __shared__ __align__(128) unsigned char dyn_raw[];
+    using TA = typename Pr::TA;
+    __shared__ KParams sP;
+    const int t = blockIdx.x;
+    const int c = __ldg(T.tile_case + t);
+    const int a = (*(volatile unsigned char*)T.parity) ^ (s & 1);
+    const BatchCase& C = T.cases[c];
+    const int local = t - C.first_tile;
+    const int bx = local % C.tiles_x, by = local / C.tiles_x;
+    staged_tile_issue<N, Pr>(maps[2 * c + a], bx, by, dyn_raw);
+    load_params(sP, T.params + c);   // while the copies are in flight
+    __syncthreads();                 // staged_tile_finish reads sP from its first line
+    staged_tile_finish<N, Pr>(sP, C.pop[a], const_cast<void*>(C.pop[a ^ 1]), (const TA*)C.aux[a], (TA*)C.aux[a ^ 1],
+                              T.status, bx, by, dyn_raw);
 }
 
 }  // namespace lbm

@@ -64,6 +64,11 @@ struct lbm_batch {
     unsigned char* d_parity = nullptr;     // [NKIND]
     unsigned int* d_bar = nullptr;         // [NKIND][2]
     int* d_status = nullptr;
+    // staged form: tensor maps of every case's two sets (maps[2 c + k] over pop[k], aux[k]
+    // of the case table), and the groups whose cases all have them
+    std::vector<StageMaps> maps;
+    StageMaps* d_maps = nullptr;
+    bool group_stageable[NKIND] = {false, false, false};
     // graph of the launches of one call length, for the mode it was captured in
     cudaGraphExec_t exec = nullptr;
     long graph_steps = -1;
@@ -106,9 +111,21 @@ static void free_tables(lbm_batch* b)
     cudaFree(b->d_cases);
     cudaFree(b->d_params);
     cudaFree(b->d_tile_case);
+    cudaFree(b->d_maps);
     b->d_cases = nullptr;
     b->d_params = nullptr;
     b->d_tile_case = nullptr;
+    b->d_maps = nullptr;
+}
+
+// Tensor maps of case c's two sets as the case table holds them; false where the case
+// cannot be staged (policy, N, nx) or the driver cannot encode them.
+static bool encode_case_maps(lbm_batch* b, int c)
+{
+    const lbm_handle* h = b->h[c];
+    const BatchCase& C = b->cases[c];
+    return lbm_encode_stage_maps(h, C.pop[0], C.aux[0], &b->maps[2 * c]) &&
+           lbm_encode_stage_maps(h, C.pop[1], C.aux[1], &b->maps[2 * c + 1]);
 }
 
 // Group membership, tile lists and the case table for the current plan; the sets of
@@ -153,6 +170,12 @@ static int build_tables(lbm_batch* b)
     }
     std::vector<KParams> params(nc);
     for (int c = 0; c < nc; ++c) params[c] = b->h[c]->P;
+    // the staged form: groups of 32x8 tiles whose every case has its tensor maps
+    b->maps.assign(2 * (size_t)nc, StageMaps{});
+    const bool stage_policy = (b->precision == LBM_FP16S || b->precision == LBM_BF16S) && b->N == 2;
+    for (int g = 0; g < NKIND; ++g) b->group_stageable[g] = stage_policy && KIND_TILE[g] == TILE_32x8 && b->group_tiles[g] > 0;
+    for (int c = 0; c < nc; ++c)
+        if (b->group_stageable[b->group[c]] && !encode_case_maps(b, c)) b->group_stageable[b->group[c]] = false;
     BATCH_TRY(b, cudaSetDevice(b->device));
     BATCH_TRY(b, cudaMalloc(&b->d_cases, nc * sizeof(BatchCase)));
     BATCH_TRY(b, cudaMalloc(&b->d_params, nc * sizeof(KParams)));
@@ -161,6 +184,8 @@ static int build_tables(lbm_batch* b)
     BATCH_TRY(b, cudaMemcpy(b->d_params, params.data(), nc * sizeof(KParams), cudaMemcpyHostToDevice));
     if (!flat.empty())
         BATCH_TRY(b, cudaMemcpy(b->d_tile_case, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice));
+    BATCH_TRY(b, cudaMalloc(&b->d_maps, b->maps.size() * sizeof(StageMaps)));
+    BATCH_TRY(b, cudaMemcpy(b->d_maps, b->maps.data(), b->maps.size() * sizeof(StageMaps), cudaMemcpyHostToDevice));
     return LBM_OK;
 }
 
@@ -179,7 +204,8 @@ static BatchTable group_table(const lbm_batch* b, int g)
 }
 
 // A member handle stepped on its own (or given new fields) since the table was built:
-// re-point its sets.  Returns true when the device table must be refreshed.
+// re-point its sets (and their tensor maps).  Returns true when the device tables must be
+// refreshed.
 static bool resync_cases(lbm_batch* b)
 {
     bool dirty = false;
@@ -192,6 +218,10 @@ static bool resync_cases(lbm_batch* b)
             C.pop[p ^ 1] = h->pop[h->cur ^ 1];
             C.aux[p] = h->aux[h->cur];
             C.aux[p ^ 1] = h->aux[h->cur ^ 1];
+            if (b->group_stageable[b->group[c]] && !encode_case_maps(b, c)) {
+                b->group_stageable[b->group[c]] = false;
+                drop_graph(b);   // its launches chose the staged kernel for this group
+            }
             dirty = true;
         }
     }
@@ -238,7 +268,8 @@ __global__ void flip_parity_kernel(unsigned char* parity, int n)
     if (threadIdx.x < n) parity[threadIdx.x] ^= 1;
 }
 
-// The per-step launches of one call: one launch per group and step.
+// The per-step launches of one call: one launch per group and step (in the staged mode,
+// the staged kernel for the groups that allow it).
 static int enqueue_per_step(lbm_batch* b, int nsteps, cudaStream_t st)
 {
     for (int s = 0; s < nsteps; ++s)
@@ -246,7 +277,10 @@ static int enqueue_per_step(lbm_batch* b, int nsteps, cudaStream_t st)
             if (b->group_tiles[g] == 0) continue;
             const BatchTable T = group_table(b, g);
             const int kind = KIND_TILE[g];
+            const bool staged = b->mode == LBM_BATCH_STAGED && b->group_stageable[g];
+            const StageMaps* maps = b->d_maps;
             cudaError_t e = dispatch(b->N, b->precision, [&](auto n, auto pr) {
+                if (staged) return launch_batch_staged<decltype(n)::value, decltype(pr)>(T, maps, s, st);
                 return launch_batch_step<decltype(n)::value, decltype(pr)>(T, kind, s, st);
             });
             if (e != cudaSuccess) return bcuda(b, e, "batch step launch");
@@ -262,7 +296,7 @@ static int enqueue_per_step(lbm_batch* b, int nsteps, cudaStream_t st)
 // use, replayed afterwards), or launched directly where capture is refused.
 static int run_call(lbm_batch* b, int nsteps)
 {
-    const bool per_step = b->mode == LBM_BATCH_PER_STEP;
+    const bool per_step = b->mode != LBM_BATCH_PERSISTENT;
     bool& ok = per_step ? b->graph_ok_step : b->graph_ok;
     auto enqueue = [&](cudaStream_t st) {
         return per_step ? enqueue_per_step(b, nsteps, st) : enqueue_persistent(b, nsteps, st);
@@ -303,9 +337,12 @@ static int run_call(lbm_batch* b, int nsteps)
 static int batch_advance(lbm_batch* b, int nsteps)
 {
     if (nsteps == 0) return LBM_OK;
-    if (resync_cases(b))
+    if (resync_cases(b)) {
         BATCH_TRY(b, cudaMemcpyAsync(b->d_cases, b->cases.data(), b->ncases * sizeof(BatchCase),
                                      cudaMemcpyHostToDevice, b->stream));
+        BATCH_TRY(b, cudaMemcpyAsync(b->d_maps, b->maps.data(), b->maps.size() * sizeof(StageMaps),
+                                     cudaMemcpyHostToDevice, b->stream));
+    }
     const int rc = run_call(b, nsteps);
     if (rc != LBM_OK) return rc;
     for (int g = 0; g < NKIND; ++g) b->parity[g] ^= (unsigned char)(nsteps & 1);
@@ -333,8 +370,8 @@ static lbm_batch_plan current_plan(const lbm_batch* b)
 
 static int apply_plan(lbm_batch* b, const lbm_batch_plan* p)
 {
-    if (p->mode != LBM_BATCH_PERSISTENT && p->mode != LBM_BATCH_PER_STEP)
-        return bfail(b, LBM_EINVAL, "plan mode must be LBM_BATCH_PERSISTENT or LBM_BATCH_PER_STEP");
+    if (p->mode != LBM_BATCH_PERSISTENT && p->mode != LBM_BATCH_PER_STEP && p->mode != LBM_BATCH_STAGED)
+        return bfail(b, LBM_EINVAL, "plan mode must be LBM_BATCH_PERSISTENT, LBM_BATCH_PER_STEP or LBM_BATCH_STAGED");
     if (p->blocks_per_sm < 0) return bfail(b, LBM_EINVAL, "blocks_per_sm must be >= 0");
     int kinds[LBM_BATCH_CLASSES];
     for (int k = 0; k < LBM_BATCH_CLASSES; ++k) {
@@ -485,7 +522,9 @@ int lbm_batch_sync(lbm_batch* b)
     if (status != 0) {
         BATCH_TRY(b, cudaMemset(b->d_status, 0, sizeof(int)));
         BATCH_TRY(b, cudaMemset(b->d_bar, 0, 2 * NKIND * sizeof(unsigned int)));
-        return bfail(b, LBM_ETIMEOUT, "a grid-barrier wait of the persistent batch launch gave up");
+        return bfail(b, LBM_ETIMEOUT,
+                     "a bounded wait of a batch launch gave up (a grid barrier of the persistent form, or the "
+                     "tensor copies of the staged form); the state is undefined");
     }
     return LBM_OK;
 }
@@ -545,9 +584,12 @@ int lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_plan* best)
         }
         return LBM_OK;
     };
-    if (rc == LBM_OK) {
+    bool stageable = false;
+    for (int g = 0; g < NKIND; ++g) stageable = stageable || b->group_stageable[g];
+    for (int mode = LBM_BATCH_PERSISTENT; mode <= LBM_BATCH_STAGED && rc == LBM_OK; ++mode) {
+        if (mode == cur.mode || (mode == LBM_BATCH_STAGED && !stageable)) continue;
         lbm_batch_plan p = cur;
-        p.mode = cur.mode == LBM_BATCH_PERSISTENT ? LBM_BATCH_PER_STEP : LBM_BATCH_PERSISTENT;
+        p.mode = mode;
         rc = consider(p);
     }
     for (int k = 0; k < LBM_BATCH_CLASSES && rc == LBM_OK; ++k) {

@@ -119,21 +119,29 @@ static bool encode_map(CUtensorMap* m, void* base, int esz, int nx, int ny, int 
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The six maps of population set k and lagged set k (boxes A..F of lbm_staged.cuh).
+// The six maps of a population set and a lagged set (boxes A..F of lbm_staged.cuh).
 template <int N, class Pr>
-static bool encode_stage_maps(lbm_handle* h, int k, StageMaps& M)
+static bool encode_stage_maps(const lbm_handle* h, const void* pop, const void* aux, StageMaps& M)
 {
     using Lay = StageLayout<N, Pr>;
     const int nx = h->nx, ny = h->ny;
-    char* rest = (char*)h->pop[k];
+    char* rest = (char*)pop;
     char* move = rest + h->P.rest_elems * Lay::ER;
-    char* aux = (char*)h->aux[k];
+    char* lag = (char*)aux;
     return encode_map(&M.m[0], move, Lay::EM, nx, ny, 8 * (N + 2), STAGE_TX, STAGE_TY, 8) &&
            encode_map(&M.m[1], move, Lay::EM, nx, ny, 8 * (N + 2), Lay::WM, Lay::H, 8 * (N + 1)) &&
            encode_map(&M.m[2], rest, Lay::ER, nx, ny, N + 2, STAGE_TX, STAGE_TY, 1) &&
            encode_map(&M.m[3], rest, Lay::ER, nx, ny, N + 2, Lay::WR, Lay::H, N + 1) &&
-           encode_map(&M.m[4], aux, Lay::EA, nx, ny, 3 + 2 * N, Lay::WA, Lay::H, 2) &&
-           encode_map(&M.m[5], aux, Lay::EA, nx, ny, 3 + 2 * N, STAGE_TX, STAGE_TY, 1 + 2 * N);
+           encode_map(&M.m[4], lag, Lay::EA, nx, ny, 3 + 2 * N, Lay::WA, Lay::H, 2) &&
+           encode_map(&M.m[5], lag, Lay::EA, nx, ny, 3 + 2 * N, STAGE_TX, STAGE_TY, 1 + 2 * N);
+}
+
+bool lbm_encode_stage_maps(const lbm_handle* h, const void* pop, const void* aux, StageMaps* M)
+{
+    if (!h || !M || h->N != 2 || h->nx % 8 != 0) return false;
+    if (h->precision == LBM_FP16S) return encode_stage_maps<2, PrecFP16S>(h, pop, aux, *M);
+    if (h->precision == LBM_BF16S) return encode_stage_maps<2, PrecBF16S>(h, pop, aux, *M);
+    return false;
 }
 
 // Turn the staged step on where the handle allows it (see lbm_set_staging); with report,
@@ -152,9 +160,7 @@ static int enable_staging(lbm_handle* h, bool report)
         LBM_CUDA_TRY(h, cudaMemset(h->stage_status, 0, sizeof(int)));
     }
     bool ok = true;
-    for (int k = 0; k < 2 && ok; ++k)
-        ok = h->precision == LBM_FP16S ? encode_stage_maps<2, PrecFP16S>(h, k, h->stage_maps[k])
-                                       : encode_stage_maps<2, PrecBF16S>(h, k, h->stage_maps[k]);
+    for (int k = 0; k < 2 && ok; ++k) ok = lbm_encode_stage_maps(h, h->pop[k], h->aux[k], &h->stage_maps[k]);
     if (!ok) return report ? fail(h, LBM_ECUDA, "tensor maps of the staged step could not be encoded") : LBM_ECUDA;
     h->staged = true;
     return LBM_OK;

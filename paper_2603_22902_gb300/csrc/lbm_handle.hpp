@@ -37,3 +37,9 @@ struct lbm_handle {
     int slab_y0 = 0;
     std::string err;
 };
+
+// The six tensor maps of the staged step (boxes A..F of lbm_staged.cuh) over a population
+// set `pop` and a lagged set `aux` laid out like the handle's (16-bit storage, N = 2,
+// nx a multiple of 8); false when the driver cannot encode them.  Defined in lbm_capi.cu,
+// used by the handle's own staged step and by the staged batch form.
+bool lbm_encode_stage_maps(const lbm_handle* h, const void* pop, const void* aux, lbm::StageMaps* M);

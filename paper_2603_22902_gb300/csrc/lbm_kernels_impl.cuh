@@ -160,6 +160,21 @@ cudaError_t launch_batch_step(const BatchTable& T, int kind, int s, cudaStream_t
     }
 }
 
+template <int N, class Pr>
+cudaError_t launch_batch_staged(const BatchTable& T, const StageMaps* maps, int s, cudaStream_t st)
+{
+    if constexpr (staged_policy<Pr>() && N == 2) {
+        using Lay = StageLayout<N, Pr>;
+        cudaError_t e = cudaFuncSetAttribute(batch_staged_kernel<N, Pr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Lay::TOTAL);
+        if (e != cudaSuccess) return e;
+        batch_staged_kernel<N, Pr><<<T.total_tiles, STAGE_NT, Lay::TOTAL, st>>>(T, maps, s);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
 template <int N>
 cudaError_t launch_adj_mac(const KParams& P, const double* pin, const double* ain, double* mac, cudaStream_t st)
 {
@@ -213,6 +228,7 @@ cudaError_t launch_adj_init(const KParams& P, const double* phi0, const double* 
                                             long long, long long);                                                  \
     template cudaError_t launch_batch_persistent<N, PR>(const BatchTable&, int, int, int, cudaStream_t);            \
     template cudaError_t batch_blocks_per_sm<N, PR>(int, int*);                                                     \
-    template cudaError_t launch_batch_step<N, PR>(const BatchTable&, int, int, cudaStream_t);
+    template cudaError_t launch_batch_step<N, PR>(const BatchTable&, int, int, cudaStream_t);                       \
+    template cudaError_t launch_batch_staged<N, PR>(const BatchTable&, const StageMaps*, int, cudaStream_t);
 
 }  // namespace lbm

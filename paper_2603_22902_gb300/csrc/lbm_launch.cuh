@@ -93,6 +93,10 @@ cudaError_t batch_blocks_per_sm(int kind, int* out);
 // One launch of step s of the group, one block per tile.
 template <int N, class Pr>
 cudaError_t launch_batch_step(const BatchTable& T, int kind, int s, cudaStream_t st);
+// One launch of step s of a group of 32x8 tiles in the staged form (16-bit storage, N = 2;
+// cudaErrorNotSupported otherwise); maps[2 c + k]: case c, population and lagged set k.
+template <int N, class Pr>
+cudaError_t launch_batch_staged(const BatchTable& T, const StageMaps* maps, int s, cudaStream_t st);
 
 // ---- adjoint of the FP64 step (lbm_adjoint.cuh) ------------------------------------
 // Gradient slots (planes of the gradient buffer).

@@ -19,7 +19,7 @@
 // wide.  Every tile is staged this way: positions of a box beyond the lattice (left of
 // x = 0, below y = 0, past the right or top side) are filled with zeros by the copy and
 // are either never read (beyond a wall or an outflow side: the ghost rule replaces them)
-// or, across a periodic side, read again from the cells they wrap to (stage_wrap).  The
+// or, across a periodic side, read again from the cells they wrap to (wrap_item).  The
 // arithmetic is step_tile_l of the one-cell step with a loader that reads the stage, so
 // every cell is computed exactly as the one-cell step computes it (the two forms agree
 // bit for bit), and that code exists once in the kernel (a second copy for the tiles at
@@ -177,83 +177,161 @@ __device__ __forceinline__ void stage_issue(const StageMaps& M, unsigned char* s
 // its right or top side), so they are read again, with plain loads, from the cells they
 // wrap to.  Positions beyond a side that is not periodic keep the zeros (the ghost rule
 // replaces them); the own-cell boxes (A, C, F) are read only at cells of the lattice.
-// The work is one load per (position, plane): the wrapped columns (10 positions each)
-// and rows (34 each) of the tile with its ring times the 8 (N + 1) + (N + 1) + 2 planes,
-// spread over the block (a corner in both lists is read twice, to the same value).
+// The work is one load per (position, plane) item: the wrapped columns (10 positions
+// each) and rows (34 each) of the tile with its ring, times the 8 (N + 1) + (N + 1) + 2
+// planes; a corner in both lists is read twice, to the same value.  The first items of
+// each thread are loaded before the wait for the tensor copies, so that their latency
+// overlaps the copies', and stored once the copies have landed.
+struct WrapGeom {
+    int nL, cR, nB, rT, ncol, items;
+};
+
 template <int N, class Pr>
-__device__ __forceinline__ void stage_wrap(const KParams& P, const void* __restrict__ pin_base,
-                                           const typename Pr::TA* __restrict__ ain, unsigned char* st, int x0, int y0)
+__device__ __forceinline__ WrapGeom wrap_geom(const KParams& P, int x0, int y0)
+{
+    using Lay = StageLayout<N, Pr>;
+    constexpr int RW = STAGE_TX + 2, PLANES = 9 * (N + 1) + 2;
+    const bool xper = P.bc[0] == PERIODIC, yper = P.bc[2] == PERIODIC;
+    WrapGeom G;
+    // wrapped columns: lx = 0 (x0 = 0) and lx = cR .. RW - 1 (past the right side);
+    // wrapped rows: ly = 0 (y0 = 0) and ly = rT .. H - 1 (past the top side)
+    G.nL = xper && x0 == 0 ? 1 : 0;
+    G.cR = P.nx - x0 + 1;
+    const int nR = xper && G.cR < RW ? RW - G.cR : 0;
+    G.nB = yper && y0 == 0 ? 1 : 0;
+    G.rT = P.ny - y0 + 1;
+    const int nT = yper && G.rT < Lay::H ? Lay::H - G.rT : 0;
+    G.ncol = (G.nL + nR) * Lay::H;
+    G.items = (G.ncol + (G.nB + nT) * RW) * PLANES;
+    return G;
+}
+
+template <class T>
+__device__ __forceinline__ unsigned raw_bits(T v)
+{
+    static_assert(sizeof(T) == 2 || sizeof(T) == 4, "staged elements are 2 or 4 bytes");
+    if constexpr (sizeof(T) == 2) {
+        unsigned short u;
+        memcpy(&u, &v, 2);
+        return u;
+    } else {
+        unsigned u;
+        memcpy(&u, &v, 4);
+        return u;
+    }
+}
+
+// Item e: its byte offset in the stage and the bits of its value; false for a position
+// beyond a side that is not periodic (nothing to write).
+template <int N, class Pr>
+__device__ __forceinline__ bool wrap_item(const KParams& P, const PopView<Pr>& v, const typename Pr::TA* __restrict__ ain,
+                                          int x0, int y0, const WrapGeom& G, int e, unsigned& off, unsigned& bits)
 {
     using Lay = StageLayout<N, Pr>;
     using TR = typename Pr::TR;
     using TM = typename Pr::TM;
     using TA = typename Pr::TA;
-    const PopView<Pr> v = pop_view<Pr>(P, pin_base);
+    constexpr int RW = STAGE_TX + 2, PLANES = 9 * (N + 1) + 2;
     const int nx = P.nx, ny = P.ny;
     const long long S = P.S;
-    const bool xper = P.bc[0] == PERIODIC, yper = P.bc[2] == PERIODIC;
-    constexpr int RW = STAGE_TX + 2, PLANES = 9 * (N + 1) + 2;
-    // wrapped columns: lx = 0 (x0 = 0) and lx = cR .. RW - 1 (past the right side);
-    // wrapped rows: ly = 0 (y0 = 0) and ly = rT .. H - 1 (past the top side)
-    const int nL = xper && x0 == 0 ? 1 : 0, cR = nx - x0 + 1, nR = xper && cR < RW ? RW - cR : 0;
-    const int nB = yper && y0 == 0 ? 1 : 0, rT = ny - y0 + 1, nT = yper && rT < Lay::H ? Lay::H - rT : 0;
-    const int ncol = (nL + nR) * Lay::H, items = (ncol + (nB + nT) * RW) * PLANES;
-    TM* B = reinterpret_cast<TM*>(st + Lay::OB);
-    TR* D = reinterpret_cast<TR*>(st + Lay::OD);
-    TA* E = reinterpret_cast<TA*>(st + Lay::OE);
-    for (int e = threadIdx.x; e < items; e += STAGE_NT) {
-        const int pl = e % PLANES, pos = e / PLANES;
-        int lx, ly;
-        if (pos < ncol) {
-            const int k = pos / Lay::H;
-            ly = pos % Lay::H;
-            lx = k < nL ? 0 : cR + (k - nL);
-        } else {
-            const int k = (pos - ncol) / RW;
-            lx = (pos - ncol) % RW;
-            ly = k < nB ? 0 : rT + (k - nB);
-        }
-        int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        const bool xout = gx < 0 || gx >= nx, yout = gy < 0 || gy >= ny;
-        if ((xout && !xper) || (yout && !yper)) continue;   // beyond a wall or an outflow side
-        if (xout) gx = wrap_index(gx, nx);
-        if (yout) gy = wrap_index(gy, ny);
-        const long long c = (long long)gy * nx + gx;
-        if (pl < 8 * (N + 1))
-            B[(pl * Lay::H + ly) * Lay::WM + lx - 1 + Lay::PM] = LBM_LD(P, v.move, (8 + pl) * S + c, P.move_elems, 43);
-        else if (pl < 9 * (N + 1))
-            D[((pl - 8 * (N + 1)) * Lay::H + ly) * Lay::WR + lx - 1 + Lay::PR] =
-                LBM_LD(P, v.rest, (1 + pl - 8 * (N + 1)) * S + c, P.rest_elems, 44);
-        else
-            E[((pl - 9 * (N + 1)) * Lay::H + ly) * Lay::WA + lx - 1 + Lay::PA] =
-                LBM_LD(P, ain, (pl - 9 * (N + 1)) * S + c, P.aux_elems, 45);
+    const int pl = e % PLANES, pos = e / PLANES;
+    int lx, ly;
+    if (pos < G.ncol) {
+        const int k = pos / Lay::H;
+        ly = pos % Lay::H;
+        lx = k < G.nL ? 0 : G.cR + (k - G.nL);
+    } else {
+        const int k = (pos - G.ncol) / RW;
+        lx = (pos - G.ncol) % RW;
+        ly = k < G.nB ? 0 : G.rT + (k - G.nB);
+    }
+    int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    const bool xout = gx < 0 || gx >= nx, yout = gy < 0 || gy >= ny;
+    if ((xout && P.bc[0] != PERIODIC) || (yout && P.bc[2] != PERIODIC)) return false;
+    if (xout) gx = wrap_index(gx, nx);
+    if (yout) gy = wrap_index(gy, ny);
+    const long long c = (long long)gy * nx + gx;
+    if (pl < 8 * (N + 1)) {
+        off = Lay::OB + ((pl * Lay::H + ly) * Lay::WM + lx - 1 + Lay::PM) * (unsigned)sizeof(TM);
+        bits = raw_bits(LBM_LD(P, v.move, (8 + pl) * S + c, P.move_elems, 43));
+    } else if (pl < 9 * (N + 1)) {
+        const int s = pl - 8 * (N + 1);
+        off = Lay::OD + ((s * Lay::H + ly) * Lay::WR + lx - 1 + Lay::PR) * (unsigned)sizeof(TR);
+        bits = raw_bits(LBM_LD(P, v.rest, (1 + s) * S + c, P.rest_elems, 44));
+    } else {
+        const int a = pl - 9 * (N + 1);
+        off = Lay::OE + ((a * Lay::H + ly) * Lay::WA + lx - 1 + Lay::PA) * (unsigned)sizeof(TA);
+        bits = raw_bits(LBM_LD(P, ain, a * S + c, P.aux_elems, 45));
+    }
+    return true;
+}
+
+template <int N, class Pr>
+__device__ __forceinline__ void wrap_store(unsigned char* st, unsigned off, unsigned bits)
+{
+    using Lay = StageLayout<N, Pr>;
+    static_assert(sizeof(typename Pr::TR) == 4 && sizeof(typename Pr::TA) == 4, "the ring boxes D, E hold 4-byte values");
+    if (off < (unsigned)Lay::OC) {
+        if constexpr (sizeof(typename Pr::TM) == 2) *reinterpret_cast<unsigned short*>(st + off) = (unsigned short)bits;
+        else *reinterpret_cast<unsigned*>(st + off) = bits;
+    } else {
+        *reinterpret_cast<unsigned*>(st + off) = bits;
     }
 }
 
-// One step: one block per tile (a one-dimensional grid of all tiles, up to four blocks
-// per SM, the tiles at the sides first).  Every tile is computed from its stage in shared
-// memory, so the step's arithmetic is compiled once: thread 0 issues the tile's six tensor
-// copies, every thread waits for them, and a tile at a periodic side then reads its
-// wrapped positions again (stage_wrap).
+// The staged step of tile (bx, by), run by a block of STAGE_NT threads whose dynamic
+// shared memory `dyn_raw` holds StageLayout<N, Pr>::TOTAL bytes, in two parts:
+//   staged_tile_issue: thread 0 initialises the mbarrier and issues the tile's six tensor
+//     copies (the caller may do other work, such as loading the parameter block, while
+//     they are in flight);
+//   staged_tile_finish (P must be complete and visible to every thread on entry: it is
+//     read before the first block barrier): every thread waits for the copies (a block
+//     barrier first, so the mbarrier is initialised before anyone waits on it), a tile at
+//     a periodic side then writes its wrapped positions over the copies' zeros
+//     (wrap_item), and the tile is computed from the stage.  Every tile is computed this
+//     way, so the step's arithmetic is compiled once.
+__device__ __forceinline__ unsigned char* stage_base(unsigned char* dyn_raw)
+{
+    return dyn_raw + ((128u - (smem_addr(dyn_raw) & 127u)) & 127u);
+}
+
 template <int N, class Pr>
-__global__ void __launch_bounds__(STAGE_NT, 4)
-staged_tile_kernel(const KParams P, const __grid_constant__ StageMaps M, const void* __restrict__ pin_base,
-                   void* __restrict__ pout_base, const typename Pr::TA* __restrict__ ain,
-                   typename Pr::TA* __restrict__ aout, int* __restrict__ status)
+__device__ __forceinline__ void staged_tile_issue(const StageMaps& M, int bx, int by, unsigned char* dyn_raw)
 {
     using Lay = StageLayout<N, Pr>;
-    using R = typename Pr::R;
-    extern __shared__ __align__(128) unsigned char dyn_raw[];
-    unsigned char* dyn = dyn_raw + ((128u - (smem_addr(dyn_raw) & 127u)) & 127u);
-    R* one = reinterpret_cast<R*>(dyn + Lay::OONE);
-    int bx, by;
-    ring_first_tile(blockIdx.x, (P.nx + STAGE_TX - 1) / STAGE_TX, (P.ny + STAGE_TY - 1) / STAGE_TY, bx, by);
-    const int x0 = bx * STAGE_TX, y0 = by * STAGE_TY;
-    const unsigned bar = smem_addr(dyn + Lay::OBAR);
+    unsigned char* dyn = stage_base(dyn_raw);
     if (threadIdx.x == 0) {
+        const unsigned bar = smem_addr(dyn + Lay::OBAR);
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         stage_issue<N, Pr>(M, dyn, bar, bx, by);
+    }
+}
+
+template <int N, class Pr>
+__device__ __forceinline__ void staged_tile_finish(const KParams& P, const void* __restrict__ pin_base,
+                                                   void* __restrict__ pout_base,
+                                                   const typename Pr::TA* __restrict__ ain,
+                                                   typename Pr::TA* __restrict__ aout, int* __restrict__ status,
+                                                   int bx, int by, unsigned char* dyn_raw)
+{
+    using Lay = StageLayout<N, Pr>;
+    using R = typename Pr::R;
+    unsigned char* dyn = stage_base(dyn_raw);
+    R* one = reinterpret_cast<R*>(dyn + Lay::OONE);
+    const int x0 = bx * STAGE_TX, y0 = by * STAGE_TY;
+    const unsigned bar = smem_addr(dyn + Lay::OBAR);
+    const bool wraps = (P.bc[0] == PERIODIC && (x0 == 0 || x0 + STAGE_TX >= P.nx)) ||
+                       (P.bc[2] == PERIODIC && (y0 == 0 || y0 + STAGE_TY >= P.ny));
+    WrapGeom G{};
+    unsigned off0 = 0, bits0 = 0, off1 = 0, bits1 = 0;
+    bool has0 = false, has1 = false;
+    if (wraps) {   // the first two items of this thread, loaded while the copies are in flight
+        const PopView<Pr> v = pop_view<Pr>(P, pin_base);
+        G = wrap_geom<N, Pr>(P, x0, y0);
+        const int e0 = threadIdx.x, e1 = threadIdx.x + STAGE_NT;
+        if (e0 < G.items) has0 = wrap_item<N, Pr>(P, v, ain, x0, y0, G, e0, off0, bits0);
+        if (e1 < G.items) has1 = wrap_item<N, Pr>(P, v, ain, x0, y0, G, e1, off1, bits1);
     }
     __syncthreads();   // the mbarrier is initialised before anyone waits on it
     const bool ok = mbar_wait(bar, 0);
@@ -267,14 +345,33 @@ staged_tile_kernel(const KParams P, const __grid_constant__ StageMaps M, const v
         return;
     }
     const bool inside = ring_inside(P, x0, y0);
-    const bool wraps = (P.bc[0] == PERIODIC && (x0 == 0 || x0 + STAGE_TX >= P.nx)) ||
-                       (P.bc[2] == PERIODIC && (y0 == 0 || y0 + STAGE_TY >= P.ny));
-    if (wraps) {
-        stage_wrap<N, Pr>(P, pin_base, ain, dyn, x0, y0);
+    if (wraps) {   // the wrapped positions over the copies' zeros
+        if (has0) wrap_store<N, Pr>(dyn, off0, bits0);
+        if (has1) wrap_store<N, Pr>(dyn, off1, bits1);
+        const PopView<Pr> v = pop_view<Pr>(P, pin_base);
+        for (int e = threadIdx.x + 2 * STAGE_NT; e < G.items; e += STAGE_NT) {
+            unsigned off, bits;
+            if (wrap_item<N, Pr>(P, v, ain, x0, y0, G, e, off, bits)) wrap_store<N, Pr>(dyn, off, bits);
+        }
         __syncthreads();
     }
     const StagedLoader<N, Pr> ld{P, dyn, x0, y0, !inside};
     step_tile_l<N, STAGE_TX, STAGE_TY, true, Pr>(P, ld, pout_base, aout, ExportPtrs{}, bx, by, one);
+}
+
+// One step of one lattice: one block per tile (a one-dimensional grid of all tiles, up to
+// four blocks per SM, the tiles at the sides first).
+template <int N, class Pr>
+__global__ void __launch_bounds__(STAGE_NT, 4)
+staged_tile_kernel(const KParams P, const __grid_constant__ StageMaps M, const void* __restrict__ pin_base,
+                   void* __restrict__ pout_base, const typename Pr::TA* __restrict__ ain,
+                   typename Pr::TA* __restrict__ aout, int* __restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char dyn_raw[];
+    int bx, by;
+    ring_first_tile(blockIdx.x, (P.nx + STAGE_TX - 1) / STAGE_TX, (P.ny + STAGE_TY - 1) / STAGE_TY, bx, by);
+    staged_tile_issue<N, Pr>(M, bx, by, dyn_raw);
+    staged_tile_finish<N, Pr>(P, pin_base, pout_base, ain, aout, status, bx, by, dyn_raw);
 }
 
 }  // namespace lbm

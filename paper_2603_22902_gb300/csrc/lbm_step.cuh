@@ -133,7 +133,7 @@ __device__ __forceinline__ void st_pop(const KParams& P, const PopView<Pr>& v, i
 // Cell value and gives its populations (dequantised) and lagged values.
 //   GlobalLoader: the population and lagged sets in global memory, cells by their index in
 //     the lattice (step_tile_l maps a position of the tile-with-ring to it).
-//   StagedLoader: the same inputs of one interior tile copied into shared memory by the
+//   StagedLoader: the same inputs of one tile copied into shared memory by the
 //     tensor-memory accelerator (lbm_staged.cuh); cells by their position in the tile.
 template <class Pr>
 struct GlobalLoader {
@@ -368,19 +368,33 @@ __device__ __forceinline__ void push_row_at(const KParams& P, const PopView<Pr>&
     st_pop<Pr, KIND>(P, out, s, j, (long long)y * P.nx + tx, v, 13);
 }
 
-// All nine pushes of one species, plus the outflow copies of the boundary rows.  In a
-// tile whose cells and one-cell ring all lie inside the lattice (`interior`, the same for
-// the whole block), every population lands in the neighbour c + c_J: no wrap and no
-// boundary rule, so the general path's checks are skipped.
+// All nine pushes of one species, plus the outflow copies of the boundary rows.  Three
+// paths, chosen per cell by the caller:
+//   PUSH_INTERIOR: the cell's row is neither the lattice's first nor its last, and its
+//     tile's columns and their ring lie inside the lattice: every population lands in the
+//     neighbour c + c_J, no wrap and no boundary rule;
+//   PUSH_XWRAP: the cell's row is neither the first nor the last, and x is periodic: the
+//     neighbour c + c_J with its x taken modulo nx, no boundary rule;
+//   PUSH_GENERAL: the checks of push() for every population.
+constexpr int PUSH_GENERAL = 0, PUSH_INTERIOR = 1, PUSH_XWRAP = 2;
 template <int KIND, class Pr>
 __device__ __forceinline__ void push_species(const KParams& P, const PopView<Pr>& out, int s, int x, int y,
-                                             bool interior, const typename Pr::R (&q)[9])
+                                             int path, const typename Pr::R (&q)[9])
 {
-    if (interior) {
+    if (path == PUSH_INTERIOR) {
         const long long c = (long long)y * P.nx + x;
         st_pop<Pr, KIND>(P, out, s, 0, c, q[0], 10);
 #pragma unroll
         for (int j = 1; j < 9; ++j) st_pop<Pr, KIND>(P, out, s, j, c + (cy(j) * P.nx + cx(j)), q[j], 10);
+        return;
+    }
+    if (path == PUSH_XWRAP) {
+        const long long row = (long long)y * P.nx;
+        const int xm = x == 0 ? P.nx - 1 : x - 1, xp = x == P.nx - 1 ? 0 : x + 1;
+        st_pop<Pr, KIND>(P, out, s, 0, row + x, q[0], 10);
+#pragma unroll
+        for (int j = 1; j < 9; ++j)
+            st_pop<Pr, KIND>(P, out, s, j, row + cy(j) * P.nx + (cx(j) < 0 ? xm : (cx(j) > 0 ? xp : x)), q[j], 10);
         return;
     }
     push<0, KIND, Pr>(P, out, s, x, y, q[0]);
@@ -703,8 +717,13 @@ __device__ __forceinline__ void step_tile_l(const KParams& P, const L& ld, void*
         return;
     }
     const PopView<Pr> pout = pop_view<Pr>(P, pout_base);
-    // the tile and its one-cell ring inside the lattice: pushes need no boundary rule
-    const bool interior = x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1;
+    // the push path of this cell (push_species): the same for a row of the tile, so for a
+    // warp of a 32-wide tile; only the lattice's first and last rows, and columns at a
+    // side that is not periodic, take the general path
+    const bool row_inside = y >= 1 && y <= ny - 2;
+    const int path = row_inside && x0 >= 1 && x0 + TX <= nx - 1 ? PUSH_INTERIOR
+                     : row_inside && xper                         ? PUSH_XWRAP
+                                                                  : PUSH_GENERAL;
 
     // ---- stage F: flow collision -------------------------------------------
     {
@@ -731,7 +750,7 @@ __device__ __forceinline__ void step_tile_l(const KParams& P, const L& ld, void*
         R q[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) q[i] = rfma(wgt_r<R>(i), X[i], om1 * f[i]);
-        push_species<KIND_F, Pr>(P, pout, 0, x, y, interior, q);
+        push_species<KIND_F, Pr>(P, pout, 0, x, y, path, q);
     }
 
     // ---- stage F: phase-field collisions -------------------------------------
@@ -757,7 +776,7 @@ __device__ __forceinline__ void step_tile_l(const KParams& P, const L& ld, void*
             q[7] = rfma(wgt_r<R>(7), b0 - (bxv + byv), og1 * gq[7]);
             q[6] = rfma(wgt_r<R>(6), b0 + (byv - bxv), og1 * gq[6]);
             q[8] = rfma(wgt_r<R>(8), b0 - (byv - bxv), og1 * gq[8]);
-            push_species<KIND_G, Pr>(P, pout, 1 + pp, x, y, interior, q);
+            push_species<KIND_G, Pr>(P, pout, 1 + pp, x, y, path, q);
             LBM_ST(P, aout, aux_phiux(pp) * S + c, P.aux_elems, 30, (TA)(phi[pp] * ux));
             LBM_ST(P, aout, aux_phiuy(N, pp) * S + c, P.aux_elems, 31, (TA)(phi[pp] * uy));
         }
@@ -789,7 +808,7 @@ __device__ __forceinline__ void step_tile_l(const KParams& P, const L& ld, void*
         q[8] = rfma(wgt_r<R>(8), (bd - cxy) - (cyv - cxv), oh1 * h[8]);
         // outflow rows are copied inside push_species; Dirichlet rows get their
         // incoming populations from the ghost rule below
-        push_species<KIND_H, Pr>(P, pout, N + 1, x, y, interior, q);
+        push_species<KIND_H, Pr>(P, pout, N + 1, x, y, path, q);
         // Dirichlet wall: ghost behind the half-way wall with T_g = 2 T_w - T, u = 0; its
         // post-collision population is h_eq(ghost) + (1 - 1/tau_h)(h_j - h_eq_j) for the
         // three directions j that enter the boundary row (one code path for both walls:

@@ -61,7 +61,8 @@ class lbm_diag(ctypes.Structure):
                 ("nonfinite", ctypes.c_longlong), ("steps", ctypes.c_longlong)]
 
 
-LBM_BATCH_PERSISTENT, LBM_BATCH_PER_STEP = 0, 1
+LBM_BATCH_PERSISTENT, LBM_BATCH_PER_STEP, LBM_BATCH_STAGED = 0, 1, 2
+_BATCH_MODES = {"persistent": LBM_BATCH_PERSISTENT, "per_step": LBM_BATCH_PER_STEP, "staged": LBM_BATCH_STAGED}
 BATCH_CLASSES = 4
 
 
@@ -70,7 +71,7 @@ class lbm_batch_plan(ctypes.Structure):
                 ("tile", (ctypes.c_int * 2) * BATCH_CLASSES), ("graph", ctypes.c_int)]
 
     def as_dict(self):
-        return {"mode": "persistent" if self.mode == LBM_BATCH_PERSISTENT else "per_step",
+        return {"mode": {v: k for k, v in _BATCH_MODES.items()}.get(self.mode, self.mode),
                 "blocks_per_sm": self.blocks_per_sm, "tile": [tuple(t) for t in self.tile],
                 "graph": bool(self.graph)}
 
@@ -501,7 +502,7 @@ class Batch:
     def set_plan(self, mode=None, blocks_per_sm=None, tiles=None):
         p = lbm_batch_get_plan(self.b)
         if mode is not None:
-            p.mode = {"persistent": LBM_BATCH_PERSISTENT, "per_step": LBM_BATCH_PER_STEP}.get(mode, mode)
+            p.mode = _BATCH_MODES.get(mode, mode)
         if blocks_per_sm is not None:
             p.blocks_per_sm = blocks_per_sm
         if tiles is not None:

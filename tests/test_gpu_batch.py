@@ -5,7 +5,9 @@ one case through the batch must match the CPU oracle to the 1e-10 parity bar.  B
 launch forms, all three tile shapes, odd step counts in both forms (each call is replayed
 as a captured graph; the persistent launch flips its own parity, the per-step form ends an
 odd call with a parity-flip kernel), members stepped alone between batch steps, and the
-autotuner's restoration of the state are covered."""
+autotuner's restoration of the state are covered.  The staged form (16-bit storage, N = 2,
+32x8 tiles) runs the staged step's arithmetic: its cases must match the per-step form's
+and the single runs' to one unit of the 16-bit format, like the per-step form."""
 import numpy as np
 import pytest
 
@@ -78,8 +80,9 @@ def test_batch_case_against_oracle(lbm):
         s.close()
 
 
-@pytest.mark.parametrize("mode", ["persistent", "per_step"])
+@pytest.mark.parametrize("mode", ["persistent", "per_step", "staged"])
 def test_batch_odd_calls_graph_replay_and_member_steps(lbm, mode):
+    # (FP64 cases: the staged mode runs its groups in the per-step form)
     cases = W.small_batch()
     ref = singles(lbm, cases, 9)
     solvers = [lbm.Solver(c).set_fields() for c in cases]
@@ -102,7 +105,7 @@ def test_batch_odd_calls_graph_replay_and_member_steps(lbm, mode):
         assert e <= 1e-12, (c.name, e)
     plan = b.plan.as_dict()
     print(mode, plan)
-    if mode == "per_step":
+    if mode != "persistent":
         assert plan["graph"]       # the per-step calls replay a captured graph
     b.close()
     for s in solvers:
@@ -146,6 +149,72 @@ def test_reduced_precision_batch_matches_single_runs(lbm, prec):
     for s, c, R in zip(solvers, cases, ref):
         e = max_err(s.fields_numpy(), R)
         assert e <= bound, (c.name, prec, e)
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def stageable_batch():
+    """FP16-storage cases whose nx are multiples of 8 (every size class of a 32x8 group
+    can be staged), with walls, outflow, periodic sides and ragged tiles."""
+    return [W.sessile_cap(48, 40, 14.0, theta=70.0, ste=0.2, T_wall=-1.5),
+            W.film(nx=16, ny=64, h0=32.0),
+            W.periodic_drop(n=40, R=9.0, ny=29),
+            W.sessile_cap(72, 44, 16.0, theta=120.0, ste=0.08, T_wall=-0.7),
+            W.sessile_cap(136, 33, 12.0, theta=95.0, ste=0.4, T_wall=-2.0)]
+
+
+@pytest.mark.parametrize("prec", ["fp16s", "bf16s"])
+def test_staged_batch_equals_per_step_and_single_runs(lbm, prec):
+    cases = stageable_batch()
+    ref = singles(lbm, cases, 31, prec)      # single handles: the staged step by default
+    out = {}
+    for mode in ("per_step", "staged"):
+        solvers = [lbm.Solver(c, precision=prec).set_fields() for c in cases]
+        b = lbm.Batch(solvers).set_plan(mode=mode, tiles=[(32, 8)] * lbm.BATCH_CLASSES)
+        b.step(10).step(10)                  # the second call replays the captured graph
+        solvers[1].step(1)                   # a member stepped on its own between calls
+        b.step(11).sync()
+        plan = b.plan.as_dict()
+        assert plan["mode"] == mode and plan["graph"], plan
+        out[mode] = [s.fields_numpy() for s in solvers]
+        steps = [s.steps for s in solvers]
+        assert steps == [31, 32, 31, 31, 31], steps
+        b.close()
+        for s in solvers:
+            s.close()
+    # another instantiation may fuse a different FP32 multiply-add, and a 16-bit store
+    # then moves by one unit of the format (the bound of the per-step form's test)
+    for k, (A, B_) in enumerate(zip(out["per_step"], out["staged"])):
+        e = max_err(A, B_)
+        print(cases[k].name, "staged vs per-step", e)
+        assert e <= 2e-2, (cases[k].name, e)
+    for k in (0, 2, 3, 4):                   # the members stepped by the batch only
+        e = max_err(out["staged"][k], ref[k])
+        print(cases[k].name, "staged batch vs single", e)
+        assert e <= 2e-2, (cases[k].name, e)
+
+
+def test_staged_batch_autotune_and_fallback(lbm):
+    # the autotuner considers the staged form where a group allows it; a 32x8 group with
+    # a case whose nx is not a multiple of 8 runs the per-step form in the staged mode
+    cases = stageable_batch()
+    solvers = [lbm.Solver(c, precision="fp16s").set_fields() for c in cases]
+    b = lbm.Batch(solvers)
+    plan = b.autotune(trial_steps=4)
+    print("autotuned plan", plan)
+    assert plan["mode"] in ("persistent", "per_step", "staged")
+    b.close()
+    for s in solvers:
+        s.close()
+    mixed = cases[:2] + [W.periodic_drop(n=37, R=9.0, ny=29)]
+    ref = singles(lbm, mixed, 12, "fp16s")
+    solvers = [lbm.Solver(c, precision="fp16s").set_fields() for c in mixed]
+    b = lbm.Batch(solvers).set_plan(mode="staged", tiles=[(32, 8)] * lbm.BATCH_CLASSES)
+    b.step(12).sync()
+    for s, c, R in zip(solvers, mixed, ref):
+        e = max_err(s.fields_numpy(), R)
+        assert e <= 2e-2, (c.name, e)
     b.close()
     for s in solvers:
         s.close()
