@@ -652,7 +652,11 @@ def run_batch(args):
     solvers = [lbm.Solver(c, precision=prec).set_fields() for c in cases]
     batch = lbm.Batch(solvers)
     t0 = time.perf_counter()
-    plan = batch.autotune(trial_steps=args.batch_chunk) if args.autotune else batch.plan.as_dict()
+    if args.batch_mode:
+        batch.set_plan(mode=args.batch_mode, tiles=[(32, 8)] * lbm.BATCH_CLASSES)
+        plan = batch.plan.as_dict()
+    else:
+        plan = batch.autotune(trial_steps=args.batch_chunk) if args.autotune else batch.plan.as_dict()
     tune_s = time.perf_counter() - t0
     chunk = args.batch_chunk
     calls = max(1, args.steps // chunk)
@@ -744,6 +748,8 @@ def main(argv=None):
     ap.add_argument("--batch-chunk", type=int, default=10, help="steps per batch call (batch_sweep_256)")
     ap.add_argument("--batch-fp64", action="store_true", help="run the batch sweep in FP64")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--batch-mode", default=None, choices=["persistent", "per_step", "staged"],
+                    help="batch_sweep_256: this launch form with 32x8 tiles instead of the autotuner's plan")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -25,6 +25,10 @@
  *    it passes.  Calls on one handle are not thread-safe; work is stream-ordered.
  *  - No CPU fallback: without a CUDA device every call that needs one fails with
  *    LBM_ECUDA.
+ *  - Tracing: the calls that put work on the GPU (lbm_step, lbm_set_fields,
+ *    lbm_get_fields, lbm_get_diagnostics, lbm_save_state / lbm_load_state, the batch,
+ *    slab and adjoint calls) are NVTX ranges named after the call, in the NVTX domain
+ *    "lbm"; a profiler can select a call's kernels by them.
  */
 #ifndef LBM_H
 #define LBM_H

@@ -33,7 +33,7 @@ def _sources_digest(extra=()) -> str:
     h = hashlib.sha256()
     for d in (CSRC, os.path.join(ROOT, "include")):
         for name in sorted(os.listdir(d)):
-            if name.endswith((".cu", ".cuh", ".h")):
+            if name.endswith((".cu", ".cuh", ".h", ".hpp")):
                 with open(os.path.join(d, name), "rb") as fh:
                     h.update(name.encode() + fh.read())
     h.update(" ".join(ARCH + FLAGS + list(extra)).encode())

@@ -10,6 +10,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_handle.hpp"
+#include "lbm_trace.hpp"
 #include "lbm_launch.cuh"
 
 using namespace lbm;
@@ -106,6 +107,7 @@ extern "C" int lbm_adjoint_fl_loss(lbm_handle* h, const double* phi0, const doub
                                    const double* uy0, const double* fl_target, const double* weight, int where,
                                    long nsteps, int checkpoint_every, lbm_fl_grad* out)
 {
+    const lbm::TraceRange trace_range("lbm_adjoint_fl_loss");
     if (!h) return LBM_EINVAL;
     if (!phi0 || !T0 || !fl_target || !out) return afail(h, LBM_EINVAL, "phi0, T0, fl_target and out are required");
     if (where != LBM_HOST && where != LBM_DEVICE) return afail(h, LBM_EINVAL, "bad where");

@@ -10,6 +10,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_handle.hpp"
+#include "lbm_trace.hpp"
 #include "lbm_launch.cuh"
 
 using namespace lbm;
@@ -497,6 +498,7 @@ int lbm_batch_get_plan(const lbm_batch* b, lbm_batch_plan* plan)
 
 int lbm_batch_step(lbm_batch* b, long nsteps)
 {
+    const lbm::TraceRange trace_range("lbm_batch_step");
     if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
     if (nsteps < 0) return bfail(b, LBM_EINVAL, "nsteps must be >= 0");
     for (int c = 0; c < b->ncases; ++c)
@@ -531,6 +533,7 @@ int lbm_batch_sync(lbm_batch* b)
 
 int lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_plan* best)
 {
+    const lbm::TraceRange trace_range("lbm_batch_autotune");
     if (!b) return bfail(nullptr, LBM_EINVAL, "NULL batch");
     if (trial_steps < 1) return bfail(b, LBM_EINVAL, "trial_steps must be >= 1");
     BATCH_TRY(b, cudaSetDevice(b->device));

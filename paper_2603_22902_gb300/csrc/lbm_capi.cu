@@ -12,6 +12,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_handle.hpp"
+#include "lbm_trace.hpp"
 #include "lbm_launch.cuh"
 #include "lbm_staged.cuh"
 
@@ -350,6 +351,7 @@ int lbm_set_staging(lbm_handle* h, int on)
 
 int lbm_set_fields(lbm_handle* h, const double* phi, const double* T, const double* ux, const double* uy, int where)
 {
+    const lbm::TraceRange trace_range("lbm_set_fields");
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
     if (!phi || !T) return fail(h, LBM_EINVAL, "phi and T are required");
     if (where != LBM_HOST && where != LBM_DEVICE) return fail(h, LBM_EINVAL, "bad where");
@@ -411,6 +413,7 @@ static int run_diag(lbm_handle* h, double* host_out)
 
 int lbm_step(lbm_handle* h, long nsteps)
 {
+    const lbm::TraceRange trace_range("lbm_step");
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
     if (!h->ready) return fail(h, LBM_ESTATE, "lbm_set_fields has not been called");
     if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
@@ -441,6 +444,7 @@ int lbm_step(lbm_handle* h, long nsteps)
 int lbm_get_fields(lbm_handle* h, double* phi, double* T, double* H, double* fl, double* ux, double* uy, double* p,
                    int where)
 {
+    const lbm::TraceRange trace_range("lbm_get_fields");
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
     if (!h->ready) return fail(h, LBM_ESTATE, "lbm_set_fields has not been called");
     if (where != LBM_HOST && where != LBM_DEVICE) return fail(h, LBM_EINVAL, "bad where");
@@ -474,6 +478,7 @@ int lbm_get_fields(lbm_handle* h, double* phi, double* T, double* H, double* fl,
 
 int lbm_get_diagnostics(lbm_handle* h, lbm_diag* out)
 {
+    const lbm::TraceRange trace_range("lbm_get_diagnostics");
     if (!h || !out) return fail(h, LBM_EINVAL, "NULL argument");
     if (!h->ready) return fail(h, LBM_ESTATE, "lbm_set_fields has not been called");
     LBM_CUDA_TRY(h, cudaSetDevice(h->device));
@@ -493,6 +498,7 @@ int lbm_get_diagnostics(lbm_handle* h, lbm_diag* out)
 
 int lbm_save_state(lbm_handle* h, void* buf, size_t* bytes)
 {
+    const lbm::TraceRange trace_range("lbm_save_state");
     if (!h || !bytes) return fail(h, LBM_EINVAL, "NULL argument");
     const size_t need = sizeof(long long) + h->pop_bytes + h->aux_bytes;
     if (!buf) {
@@ -515,6 +521,7 @@ int lbm_save_state(lbm_handle* h, void* buf, size_t* bytes)
 
 int lbm_load_state(lbm_handle* h, const void* buf, size_t bytes)
 {
+    const lbm::TraceRange trace_range("lbm_load_state");
     if (!h || !buf) return fail(h, LBM_EINVAL, "NULL argument");
     const size_t need = sizeof(long long) + h->pop_bytes + h->aux_bytes;
     if (bytes != need) return fail(h, LBM_EINVAL, "state size does not match this handle");

@@ -27,6 +27,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_handle.hpp"
+#include "lbm_trace.hpp"
 #include "lbm_launch.cuh"
 
 using namespace lbm;
@@ -208,6 +209,7 @@ long long lbm_slab_message_bytes(const lbm_handle* h, int phase)
 
 static int slab_copy(lbm_handle* h, int side, int phase, bool pack, void* msg)
 {
+    const lbm::TraceRange trace_range(pack ? "lbm_slab_pack" : "lbm_slab_unpack");
     if (!h) return sfail(nullptr, LBM_EINVAL, "NULL handle");
     if (!msg) return sfail(h, LBM_EINVAL, "NULL message buffer");
     if (!h->ready) return sfail(h, LBM_ESTATE, "lbm_set_fields has not been called");
@@ -237,6 +239,7 @@ int lbm_slab_unpack(lbm_handle* h, int side, int phase, const void* msg)
 
 int lbm_slab_sums(lbm_handle* h, double* out)
 {
+    const lbm::TraceRange trace_range("lbm_slab_sums");
     if (!h || !out) return sfail(h, LBM_EINVAL, "NULL argument");
     if (!h->slab) return sfail(h, LBM_EINVAL, "not a slab handle");
     if (!h->ready) return sfail(h, LBM_ESTATE, "lbm_set_fields has not been called");
