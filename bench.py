@@ -514,7 +514,8 @@ def compare_precision(case, precisions, mlups_fp64, front_steps, stream, flush):
 def extra_workloads(args, lbm, stream, flush):
     """The other single-GPU configurations, timed by this same run:
     - compound_drop_1024: 1024 x 1024, N = 3, each policy timed like the headline (L2
-      flushed before every timed step, CUDA events per step);
+      flushed before every timed step, CUDA events per step), FP16 storage in its staged and
+      one-launch forms;
     - staged_fp16s: the FP16-storage step of the 512^2 and 1024^2 sessile drops in its
       TMA-staged form and in the one-launch form, timed the same way;
     - batch_sweep_256: the 256-drop sweep in one batch (FP16 storage), autotuned plan,
@@ -537,6 +538,9 @@ def extra_workloads(args, lbm, stream, flush):
             bpl = bytes_per_lu(case.N, prec)
             r[prec] = {"value": round(mlups, 2), "unit": "MLUPS", "bytes_per_lu": bpl,
                        "hbm_frac": round(bpl * mlups * 1e6 / 1e9 / hbm_peak, 4)}
+        # FP16 storage runs the TMA-staged step by default (N = 3); the one-launch form beside it
+        r["fp16s"]["form"] = "staged"
+        r["fp16s"]["one_launch"] = round(timed_mlups(lbm, case, "fp16s", 200, stream, flush, staged=False), 2)
         out["compound_drop_1024"] = r
     if "staged" in parts:
         # the FP16-storage step with its inputs staged by tensor copies against the one-launch form

@@ -199,10 +199,11 @@ int lbm_set_tile(lbm_handle* h, int bx, int by);
 /* Step with its inputs staged in shared memory by the tensor-memory accelerator: one
  * block per 32x8 tile, whose thread 0 copies the tile's populations and lagged values
  * (tile and ring) with six tensor copies; the tile is then computed from shared memory
- * (the arithmetic is that of lbm_step, cell by cell, bit for bit); tiles that touch a
- * side of the lattice are stepped from global memory.  A service of the library for
- * LBM_FP16S and LBM_BF16S handles with N = 2, nx a multiple of 8 and the 32x8 tile, where
- * it is on from lbm_create (a handle whose tensor maps cannot be encoded runs the
+ * (the arithmetic is that of lbm_step, cell by cell, bit for bit); positions beyond the
+ * lattice are filled with zeros by the copies and, across a periodic side, read again
+ * from the cells they wrap to.  A service of the library for LBM_FP16S and LBM_BF16S
+ * handles with N = 2 or 3, nx a multiple of 8 and the 32x8 tile, where it is on from
+ * lbm_create (a handle whose tensor maps cannot be encoded runs the
  * one-launch form).  on = 0 returns to the one-launch form, on = 1 asks for the staged one
  * (LBM_EINVAL where it does not apply, LBM_ECUDA when the tensor maps cannot be encoded);
  * lbm_set_tile with another shape turns it off.  Every wait for the copies is bounded; a
@@ -362,9 +363,11 @@ typedef struct lbm_batch lbm_batch;
 #define LBM_BATCH_STAGED 2     /* the per-step form, with every tile of a 32x8-tile group
                                   computed from a TMA-staged copy of its inputs (the staged
                                   step of lbm_set_staging) where the group allows it: policy
-                                  LBM_FP16S or LBM_BF16S, N = 2, every case's nx a multiple
-                                  of 8; other groups run the per-step form.  The results
-                                  equal the per-step form's bit for bit. */
+                                  LBM_FP16S or LBM_BF16S, N = 2 or 3, every case's nx a multiple
+                                  of 8; other groups run the per-step form.  Its
+                                  arithmetic is the per-step form's; the kernels are separate
+                                  instantiations, so a stored 16-bit value may differ by one
+                                  unit of the format. */
 /* Every form: the launches of a call are captured into a CUDA graph the first time a
  * call of that length runs, and the graph is replayed by later calls of that length. */
 

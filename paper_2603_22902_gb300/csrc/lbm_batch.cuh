@@ -10,7 +10,7 @@
 //     case reads what the neighbouring tiles wrote).  Loads bypass L1 (Coherent<Pr>),
 //     since the blocks read data that other blocks wrote during the same launch.
 //   * per step: one launch per step, one block per tile, read-only-path loads;
-//   * staged (16-bit storage, N = 2, 32x8 tiles): the per-step form with each tile
+//   * staged (16-bit storage, N = 2 or 3, 32x8 tiles): the per-step form with each tile
 //     computed from a TMA-staged copy of its inputs (staged_tile_issue / _finish,
 //     lbm_staged.cuh), through six tensor maps per case and set kept in global memory;
 //     the copies are in flight while the block loads the case's parameter block.
@@ -130,7 +130,7 @@ batch_step_kernel(const BatchTable T, int s)
 // Staged form: one block per tile of the flat list (32x8 tiles), step s of the call;
 // maps[2 c + k] are the tensor maps of case c's population and lagged set k.
 template <int N, class Pr>
-__global__ void __launch_bounds__(STAGE_NT, 4)
+__global__ void __launch_bounds__(STAGE_NT, stage_blocks_per_sm<N>())
 batch_staged_kernel(const BatchTable T, const StageMaps* __restrict__ maps, int s)
 {
     extern __shared__ __align__(128) unsigned char dyn_raw[];

@@ -173,7 +173,7 @@ static int build_tables(lbm_batch* b)
     for (int c = 0; c < nc; ++c) params[c] = b->h[c]->P;
     // the staged form: groups of 32x8 tiles whose every case has its tensor maps
     b->maps.assign(2 * (size_t)nc, StageMaps{});
-    const bool stage_policy = (b->precision == LBM_FP16S || b->precision == LBM_BF16S) && b->N == 2;
+    const bool stage_policy = (b->precision == LBM_FP16S || b->precision == LBM_BF16S) && (b->N == 2 || b->N == 3);
     for (int g = 0; g < NKIND; ++g) b->group_stageable[g] = stage_policy && KIND_TILE[g] == TILE_32x8 && b->group_tiles[g] > 0;
     for (int c = 0; c < nc; ++c)
         if (b->group_stageable[b->group[c]] && !encode_case_maps(b, c)) b->group_stageable[b->group[c]] = false;

@@ -139,9 +139,11 @@ static bool encode_stage_maps(const lbm_handle* h, const void* pop, const void* 
 
 bool lbm_encode_stage_maps(const lbm_handle* h, const void* pop, const void* aux, StageMaps* M)
 {
-    if (!h || !M || h->N != 2 || h->nx % 8 != 0) return false;
-    if (h->precision == LBM_FP16S) return encode_stage_maps<2, PrecFP16S>(h, pop, aux, *M);
-    if (h->precision == LBM_BF16S) return encode_stage_maps<2, PrecBF16S>(h, pop, aux, *M);
+    if (!h || !M || (h->N != 2 && h->N != 3) || h->nx % 8 != 0) return false;
+    if (h->precision == LBM_FP16S)
+        return h->N == 2 ? encode_stage_maps<2, PrecFP16S>(h, pop, aux, *M) : encode_stage_maps<3, PrecFP16S>(h, pop, aux, *M);
+    if (h->precision == LBM_BF16S)
+        return h->N == 2 ? encode_stage_maps<2, PrecBF16S>(h, pop, aux, *M) : encode_stage_maps<3, PrecBF16S>(h, pop, aux, *M);
     return false;
 }
 
@@ -149,8 +151,8 @@ bool lbm_encode_stage_maps(const lbm_handle* h, const void* pop, const void* aux
 // the reason it does not apply goes to lbm_last_error.
 static int enable_staging(lbm_handle* h, bool report)
 {
-    if ((h->precision != LBM_FP16S && h->precision != LBM_BF16S) || h->N != 2)
-        return report ? fail(h, LBM_EINVAL, "the staged step is compiled for LBM_FP16S and LBM_BF16S with N = 2")
+    if ((h->precision != LBM_FP16S && h->precision != LBM_BF16S) || (h->N != 2 && h->N != 3))
+        return report ? fail(h, LBM_EINVAL, "the staged step is compiled for LBM_FP16S and LBM_BF16S with N = 2 or 3")
                       : LBM_EINVAL;
     if (h->nx % 8 != 0)
         return report ? fail(h, LBM_EINVAL, "the staged step needs nx a multiple of 8 (16-byte rows)") : LBM_EINVAL;

@@ -63,7 +63,7 @@ template <int N, class Pr>
 cudaError_t launch_staged(const KParams& P, const StageMaps& maps, const void* pin, void* pout, const void* ain,
                           void* aout, int* status, cudaStream_t st)
 {
-    if constexpr (staged_policy<Pr>() && N == 2) {
+    if constexpr (staged_policy<Pr>() && (N == 2 || N == 3)) {
         using Lay = StageLayout<N, Pr>;
         using TA = typename Pr::TA;
         const int tiles_x = (P.nx + STAGE_TX - 1) / STAGE_TX, tiles_y = (P.ny + STAGE_TY - 1) / STAGE_TY;
@@ -163,7 +163,7 @@ cudaError_t launch_batch_step(const BatchTable& T, int kind, int s, cudaStream_t
 template <int N, class Pr>
 cudaError_t launch_batch_staged(const BatchTable& T, const StageMaps* maps, int s, cudaStream_t st)
 {
-    if constexpr (staged_policy<Pr>() && N == 2) {
+    if constexpr (staged_policy<Pr>() && (N == 2 || N == 3)) {
         using Lay = StageLayout<N, Pr>;
         cudaError_t e = cudaFuncSetAttribute(batch_staged_kernel<N, Pr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              Lay::TOTAL);

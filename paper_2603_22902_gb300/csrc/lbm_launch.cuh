@@ -35,7 +35,7 @@ template <int N, class Pr>
 cudaError_t launch_init(const KParams& P, const double* phi, const double* T, const double* ux, const double* uy,
                         void* pop, void* aux, cudaStream_t st);
 // The step with its inputs staged by the TMA (lbm_staged.cuh): policies with 16-bit moving
-// populations, N = 2, one block per tile.  maps are the six tensor maps of the input set;
+// populations, N = 2 or 3, one block per tile.  maps are the six tensor maps of the input set;
 // status receives 1 when an mbarrier wait gave up.  cudaErrorNotSupported for other policies.
 struct StageMaps {
     CUtensorMap m[6];   // boxes A..F of lbm_staged.cuh
@@ -93,7 +93,7 @@ cudaError_t batch_blocks_per_sm(int kind, int* out);
 // One launch of step s of the group, one block per tile.
 template <int N, class Pr>
 cudaError_t launch_batch_step(const BatchTable& T, int kind, int s, cudaStream_t st);
-// One launch of step s of a group of 32x8 tiles in the staged form (16-bit storage, N = 2;
+// One launch of step s of a group of 32x8 tiles in the staged form (16-bit storage, N = 2 or 3;
 // cudaErrorNotSupported otherwise); maps[2 c + k]: case c, population and lagged set k.
 template <int N, class Pr>
 cudaError_t launch_batch_staged(const BatchTable& T, const StageMaps* maps, int s, cudaStream_t st);

@@ -35,6 +35,10 @@
 namespace lbm {
 
 constexpr int STAGE_TX = 32, STAGE_TY = 8, STAGE_NT = STAGE_TX * STAGE_TY;
+// Blocks per SM the staged kernels are compiled for: the stage of N = 2 (47 KB) leaves
+// room for four, that of N = 3 (60 KB) for three.
+template <int N>
+__host__ __device__ constexpr int stage_blocks_per_sm() { return N == 2 ? 4 : 3; }
 constexpr long long STAGE_WAIT_LIMIT = 1LL << 22;   // try_wait polls of one mbarrier wait
 
 __host__ __device__ constexpr int stage_round(int b) { return (b + 127) / 128 * 128; }
@@ -359,10 +363,10 @@ __device__ __forceinline__ void staged_tile_finish(const KParams& P, const void*
     step_tile_l<N, STAGE_TX, STAGE_TY, true, Pr>(P, ld, pout_base, aout, ExportPtrs{}, bx, by, one);
 }
 
-// One step of one lattice: one block per tile (a one-dimensional grid of all tiles, up to
-// four blocks per SM, the tiles at the sides first).
+// One step of one lattice: one block per tile (a one-dimensional grid of all tiles, four
+// blocks per SM for N = 2 and three for N = 3, the tiles at the sides first).
 template <int N, class Pr>
-__global__ void __launch_bounds__(STAGE_NT, 4)
+__global__ void __launch_bounds__(STAGE_NT, stage_blocks_per_sm<N>())
 staged_tile_kernel(const KParams P, const __grid_constant__ StageMaps M, const void* __restrict__ pin_base,
                    void* __restrict__ pout_base, const typename Pr::TA* __restrict__ ain,
                    typename Pr::TA* __restrict__ aout, int* __restrict__ status)
