@@ -24,8 +24,8 @@
 //      collisions with their source terms;
 //   4. post-collision populations are pushed to the neighbours' slots of set B with
 //      the boundary rules (bounce-back, outflow copy, non-equilibrium extrapolation
-//      of the Dirichlet temperature; tiles whose ring lies inside the lattice skip the
-//      checks), and the lagged planes are written.
+//      of the Dirichlet temperature; rows that are neither the lattice's first nor its
+//      last skip the checks, see push_species), and the lagged planes are written.
 // No address outside the planes is ever formed, not even for a value that is then
 // not used: the compiler may issue loads ahead of the branch that guards them.
 #pragma once
