@@ -303,6 +303,23 @@ long long lbm_slab_message_bytes(const lbm_handle* h, int phase);
 int lbm_slab_pack(lbm_handle* h, int side, int phase, void* msg);
 int lbm_slab_unpack(lbm_handle* h, int side, int phase, const void* msg);
 
+#define LBM_SLAB_INNER 1   /* tile rows clear of the band's first two and last two rows */
+#define LBM_SLAB_EDGE 2    /* the other tile rows; completes the step */
+/* One step of a slab handle in two launches, for overlapping the halo exchange with the
+ * step: part LBM_SLAB_INNER steps the tile rows whose rows and one-cell ring avoid the
+ * band's first two and last two rows (the ghost and boundary rows that the exchange
+ * writes), part LBM_SLAB_EDGE the other tile rows, and then the step is complete (as one
+ * lbm_step: ping-pong sets flipped, step count + 1).  Each destination slot of the step is
+ * written by one cell, so the two parts together equal lbm_step bit for bit.  The
+ * exchange of step t reads and writes only the band's edge rows of the set that step t
+ * wrote, which the inner part of step t + 1 neither reads nor writes: the order per step
+ * may be inner part of step t + 1, exchange of step t (on another stream, after the edge
+ * part of step t), edge part of step t + 1 (after the exchange).  Calls out of order
+ * (LBM_SLAB_EDGE without LBM_SLAB_INNER, two LBM_SLAB_INNER, lbm_step between them) are
+ * LBM_ESTATE; a handle that is not a slab or another part is LBM_EINVAL.  Queued on the
+ * handle's stream; no synchronisation. */
+int lbm_slab_step_part(lbm_handle* h, int part);
+
 /* The diagnostics of lbm_get_diagnostics over the band's own rows, into host memory
  * out[2N + 2]: sum phi_p (N), sum (1 - f_l) phi_p (N), max |sum_p phi_p - 1| and the count of
  * non-finite cells.  Adding the sums and counts and taking the maximum of the deviation

@@ -419,6 +419,8 @@ int lbm_step(lbm_handle* h, long nsteps)
     if (!h) return fail(nullptr, LBM_EINVAL, "NULL handle");
     if (!h->ready) return fail(h, LBM_ESTATE, "lbm_set_fields has not been called");
     if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
+    if (h->slab_inner_pending)
+        return fail(h, LBM_ESTATE, "a slab step is half done: lbm_slab_step_part(LBM_SLAB_EDGE) first");
     LBM_CUDA_TRY(h, cudaSetDevice(h->device));
     for (long n = 0; n < nsteps; ++n) {
         const int a = h->cur, b = a ^ 1;

@@ -14,6 +14,20 @@ constexpr int MAXN = 4;
 constexpr int PERIODIC = 0, WALL = 1, OUTFLOW = 2;
 constexpr int ADIABATIC = 0, DIRICHLET = 1;
 
+// Which tile rows of the lattice a step launch covers: all of them (ROWS_ALL), the rows
+// [lo, hi) (ROWS_INNER), or the others (ROWS_EDGE).  A slab handle steps its inner tile
+// rows, whose cells and one-cell ring stay clear of the rows its halo exchange writes,
+// while the exchange of the previous step is in flight, and the edge rows after it.
+constexpr int ROWS_ALL = 0, ROWS_INNER = 1, ROWS_EDGE = 2;
+struct TileRows {
+    int part, lo, hi;
+};
+// Tile rows a launch covers, of ty in the lattice.
+__host__ __device__ inline int tile_rows_count(int ty, const TileRows& r)
+{
+    return r.part == ROWS_INNER ? r.hi - r.lo : r.part == ROWS_EDGE ? ty - (r.hi - r.lo) : ty;
+}
+
 // Arithmetic helpers for the compute type R of a precision policy.
 __device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }

@@ -35,6 +35,7 @@ struct lbm_handle {
     bool slab = false;
     int slab_ghost[2] = {0, 0};
     int slab_y0 = 0;
+    bool slab_inner_pending = false;      // lbm_slab_step_part: inner rows stepped, edge rows not yet
     std::string err;
 };
 

@@ -15,11 +15,13 @@ namespace lbm {
 
 template <int N, int TX, int TY, bool COLLIDE, class Pr>
 static cudaError_t launch_fused_t(const KParams& P, const void* pin, void* pout, const void* ain, void* aout,
-                                  ExportPtrs ex, cudaStream_t st)
+                                  ExportPtrs ex, cudaStream_t st, TileRows rows)
 {
     using TA = typename Pr::TA;
-    const int tiles = ((P.nx + TX - 1) / TX) * ((P.ny + TY - 1) / TY);
-    fused_step_kernel<N, TX, TY, COLLIDE, Pr><<<tiles, TX * TY, 0, st>>>(P, pin, pout, (const TA*)ain, (TA*)aout, ex);
+    const int tiles = ((P.nx + TX - 1) / TX) * tile_rows_count((P.ny + TY - 1) / TY, rows);
+    if (tiles == 0) return cudaSuccess;
+    fused_step_kernel<N, TX, TY, COLLIDE, Pr><<<tiles, TX * TY, 0, st>>>(P, pin, pout, (const TA*)ain, (TA*)aout, ex,
+                                                                         rows);
     return cudaGetLastError();
 }
 
@@ -30,25 +32,25 @@ constexpr bool single_shape() { return std::is_same<Pr, PrecDF64>::value; }
 
 template <int N, bool COLLIDE, class Pr>
 static cudaError_t launch_fused(const KParams& P, const void* pin, void* pout, const void* ain, void* aout,
-                                ExportPtrs ex, int tile, cudaStream_t st)
+                                ExportPtrs ex, int tile, cudaStream_t st, TileRows rows = TileRows{ROWS_ALL, 0, 0})
 {
     if constexpr (single_shape<Pr>()) {
-        return launch_fused_t<N, 32, 8, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
+        return launch_fused_t<N, 32, 8, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st, rows);
     } else {
         switch (tile) {
-            case TILE_32x4: return launch_fused_t<N, 32, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
-            case TILE_64x4: return launch_fused_t<N, 64, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
-            case TILE_16x16: return launch_fused_t<N, 16, 16, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
-            default: return launch_fused_t<N, 32, 8, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st);
+            case TILE_32x4: return launch_fused_t<N, 32, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st, rows);
+            case TILE_64x4: return launch_fused_t<N, 64, 4, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st, rows);
+            case TILE_16x16: return launch_fused_t<N, 16, 16, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st, rows);
+            default: return launch_fused_t<N, 32, 8, COLLIDE, Pr>(P, pin, pout, ain, aout, ex, st, rows);
         }
     }
 }
 
 template <int N, class Pr>
 cudaError_t launch_step(const KParams& P, const void* pin, void* pout, const void* ain, void* aout, int tile,
-                        cudaStream_t st)
+                        cudaStream_t st, TileRows rows)
 {
-    return launch_fused<N, true, Pr>(P, pin, pout, ain, aout, ExportPtrs{}, tile, st);
+    return launch_fused<N, true, Pr>(P, pin, pout, ain, aout, ExportPtrs{}, tile, st, rows);
 }
 
 template <int N, class Pr>
@@ -61,7 +63,7 @@ cudaError_t launch_export(const KParams& P, const void* pin, const void* ain, do
 
 template <int N, class Pr>
 cudaError_t launch_staged(const KParams& P, const StageMaps& maps, const void* pin, void* pout, const void* ain,
-                          void* aout, int* status, cudaStream_t st)
+                          void* aout, int* status, cudaStream_t st, TileRows rows)
 {
     if constexpr (staged_policy<Pr>() && (N == 2 || N == 3)) {
         using Lay = StageLayout<N, Pr>;
@@ -70,9 +72,10 @@ cudaError_t launch_staged(const KParams& P, const StageMaps& maps, const void* p
         cudaError_t e = cudaFuncSetAttribute(staged_tile_kernel<N, Pr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              Lay::TOTAL);
         if (e != cudaSuccess) return e;
-        staged_tile_kernel<N, Pr><<<tiles_x * tiles_y, STAGE_NT, Lay::TOTAL, st>>>(P, maps, pin, pout,
-                                                                                    (const TA*)ain, (TA*)aout,
-                                                                                    status);
+        const int tiles = tiles_x * tile_rows_count(tiles_y, rows);
+        if (tiles == 0) return cudaSuccess;
+        staged_tile_kernel<N, Pr><<<tiles, STAGE_NT, Lay::TOTAL, st>>>(P, maps, pin, pout, (const TA*)ain, (TA*)aout,
+                                                                        status, rows);
         return cudaGetLastError();
     } else {
         return cudaErrorNotSupported;
@@ -217,9 +220,9 @@ cudaError_t launch_adj_init(const KParams& P, const double* phi0, const double* 
 
 #define LBM_INSTANTIATE(N, PR)                                                                                      \
     template cudaError_t launch_step<N, PR>(const KParams&, const void*, void*, const void*, void*, int,           \
-                                            cudaStream_t);                                                          \
+                                            cudaStream_t, TileRows);                                                \
     template cudaError_t launch_staged<N, PR>(const KParams&, const StageMaps&, const void*, void*, const void*,   \
-                                              void*, int*, cudaStream_t);                                           \
+                                              void*, int*, cudaStream_t, TileRows);                                 \
     template cudaError_t launch_export<N, PR>(const KParams&, const void*, const void*, double*, double*, double*, \
                                               double*, double*, double*, double*, cudaStream_t);                    \
     template cudaError_t launch_init<N, PR>(const KParams&, const double*, const double*, const double*,           \

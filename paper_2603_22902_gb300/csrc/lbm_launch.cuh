@@ -27,7 +27,7 @@ inline bool tile_dims(int id, int& tx, int& ty)
 
 template <int N, class Pr>
 cudaError_t launch_step(const KParams& P, const void* pin, void* pout, const void* ain, void* aout, int tile,
-                        cudaStream_t st);
+                        cudaStream_t st, TileRows rows = TileRows{ROWS_ALL, 0, 0});
 template <int N, class Pr>
 cudaError_t launch_export(const KParams& P, const void* pin, const void* ain, double* phi, double* T, double* H,
                           double* fl, double* ux, double* uy, double* p, cudaStream_t st);
@@ -42,7 +42,7 @@ struct StageMaps {
 };
 template <int N, class Pr>
 cudaError_t launch_staged(const KParams& P, const StageMaps& maps, const void* pin, void* pout, const void* ain,
-                          void* aout, int* status, cudaStream_t st);
+                          void* aout, int* status, cudaStream_t st, TileRows rows = TileRows{ROWS_ALL, 0, 0});
 template <class Pr>
 constexpr bool staged_policy()
 {

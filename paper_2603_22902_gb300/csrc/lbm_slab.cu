@@ -21,6 +21,7 @@
 // send / receive between GPUs.  Nothing here changes the step kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -144,6 +145,20 @@ bool message_rows(const lbm_handle* h, int side, int phase, bool pack, SlabRows&
     return true;
 }
 
+// The inner tile rows of a slab handle: those whose rows and one-cell ring stay clear of
+// the band's first two and last two rows (the ghost and boundary rows its halo exchange
+// writes); the edge part is the other tile rows.
+TileRows slab_rows(const lbm_handle* h, int part)
+{
+    int tx = 32, ty = 8;
+    tile_dims(h->tile, tx, ty);
+    const int tiles_y = (h->ny + ty - 1) / ty;
+    const int lo = 1;                                              // rows >= ty, ring >= ty - 1 >= 2
+    int hi = h->ny - 3 - ty >= 0 ? (h->ny - 3 - ty) / ty + 1 : 0;  // last row + 1 (ring) <= ny - 3
+    hi = std::min(std::max(hi, lo), tiles_y);
+    return TileRows{part == LBM_SLAB_INNER ? ROWS_INNER : ROWS_EDGE, lo, hi};
+}
+
 bool slab_side_ok(const lbm_handle* h, int side)
 {
     return h->slab && (side == 2 ? h->slab_ghost[0] : side == 3 ? h->slab_ghost[1] : 0);
@@ -235,6 +250,44 @@ int lbm_slab_pack(lbm_handle* h, int side, int phase, void* msg) { return slab_c
 int lbm_slab_unpack(lbm_handle* h, int side, int phase, const void* msg)
 {
     return slab_copy(h, side, phase, false, const_cast<void*>(msg));
+}
+
+int lbm_slab_step_part(lbm_handle* h, int part)
+{
+    const lbm::TraceRange trace_range(part == LBM_SLAB_INNER ? "lbm_slab_step_part inner" : "lbm_slab_step_part edge");
+    if (!h) return sfail(nullptr, LBM_EINVAL, "NULL handle");
+    if (!h->slab) return sfail(h, LBM_EINVAL, "not a slab handle");
+    if (!h->ready) return sfail(h, LBM_ESTATE, "lbm_set_fields has not been called");
+    if (part != LBM_SLAB_INNER && part != LBM_SLAB_EDGE)
+        return sfail(h, LBM_EINVAL, "part must be LBM_SLAB_INNER or LBM_SLAB_EDGE");
+    if (part == LBM_SLAB_INNER && h->slab_inner_pending)
+        return sfail(h, LBM_ESTATE, "the inner rows of this step were stepped already: step the edge rows");
+    if (part == LBM_SLAB_EDGE && !h->slab_inner_pending)
+        return sfail(h, LBM_ESTATE, "step the inner rows of this step first");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return sfail(h, LBM_ECUDA, cudaGetErrorString(e));
+    const int a = h->cur, b = a ^ 1;
+    const TileRows rows = slab_rows(h, part);
+    e = dispatch(h->N, h->precision, [&](auto n, auto pr) {
+        if (h->staged)
+            return launch_staged<decltype(n)::value, decltype(pr)>(h->P, h->stage_maps[a], h->pop[a], h->pop[b],
+                                                                   h->aux[a], h->aux[b], h->stage_status, h->stream,
+                                                                   rows);
+        return launch_step<decltype(n)::value, decltype(pr)>(h->P, h->pop[a], h->pop[b], h->aux[a], h->aux[b],
+                                                             h->tile, h->stream, rows);
+    });
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(h, LBM_ECUDA, std::string("step kernel: ") + cudaGetErrorString(e));
+    }
+    if (part == LBM_SLAB_INNER) {
+        h->slab_inner_pending = true;
+        return LBM_OK;
+    }
+    h->slab_inner_pending = false;
+    h->cur = b;
+    h->steps++;
+    return LBM_OK;
 }
 
 int lbm_slab_sums(lbm_handle* h, double* out)

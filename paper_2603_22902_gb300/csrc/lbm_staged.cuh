@@ -369,11 +369,11 @@ template <int N, class Pr>
 __global__ void __launch_bounds__(STAGE_NT, stage_blocks_per_sm<N>())
 staged_tile_kernel(const KParams P, const __grid_constant__ StageMaps M, const void* __restrict__ pin_base,
                    void* __restrict__ pout_base, const typename Pr::TA* __restrict__ ain,
-                   typename Pr::TA* __restrict__ aout, int* __restrict__ status)
+                   typename Pr::TA* __restrict__ aout, int* __restrict__ status, TileRows rows)
 {
     extern __shared__ __align__(128) unsigned char dyn_raw[];
     int bx, by;
-    ring_first_tile(blockIdx.x, (P.nx + STAGE_TX - 1) / STAGE_TX, (P.ny + STAGE_TY - 1) / STAGE_TY, bx, by);
+    tile_of_block(blockIdx.x, (P.nx + STAGE_TX - 1) / STAGE_TX, (P.ny + STAGE_TY - 1) / STAGE_TY, rows, bx, by);
     staged_tile_issue<N, Pr>(M, bx, by, dyn_raw);
     staged_tile_finish<N, Pr>(P, pin_base, pout_base, ain, aout, status, bx, by, dyn_raw);
 }

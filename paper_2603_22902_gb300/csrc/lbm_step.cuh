@@ -878,16 +878,30 @@ __device__ __forceinline__ void ring_first_tile(int b, int tx, int ty, int& bx, 
     by = 1 + m / (tx - 2);
 }
 
-// One launch = one time step of one lattice, one block per tile (a one-dimensional grid,
-// the tiles at the sides first).
+// Tile (bx, by) of block b of a launch over the tile rows `rows` of a tx x ty tile grid:
+// all rows in the order of ring_first_tile, or the inner / edge rows in row order.
+__device__ __forceinline__ void tile_of_block(int b, int tx, int ty, const TileRows& rows, int& bx, int& by)
+{
+    if (rows.part == ROWS_ALL) {
+        ring_first_tile(b, tx, ty, bx, by);
+        return;
+    }
+    bx = b % tx;
+    const int k = b / tx;
+    by = rows.part == ROWS_INNER ? rows.lo + k : (k < rows.lo ? k : rows.hi + (k - rows.lo));
+}
+
+// One launch = one time step of one lattice (or of some of its tile rows, `rows`), one
+// block per tile (a one-dimensional grid, the tiles at the sides first).
 template <int N, int TX, int TY, bool COLLIDE, class Pr>
 __global__ void __launch_bounds__(TX * TY, (LBM_OCC(Pr) + TX * TY - 1) / (TX * TY))
 fused_step_kernel(const KParams P, const void* __restrict__ pin_base, void* __restrict__ pout_base,
-                  const typename Pr::TA* __restrict__ ain, typename Pr::TA* __restrict__ aout, ExportPtrs ex)
+                  const typename Pr::TA* __restrict__ ain, typename Pr::TA* __restrict__ aout, ExportPtrs ex,
+                  TileRows rows)
 {
     __shared__ typename Pr::R smem[tile_smem_elems<N, TX, TY, Pr>()];
     int bx, by;
-    ring_first_tile(blockIdx.x, (P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, bx, by);
+    tile_of_block(blockIdx.x, (P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, rows, bx, by);
     step_tile<N, TX, TY, COLLIDE, Pr>(P, pin_base, pout_base, ain, aout, ex, bx, by, smem);
 }
 

@@ -125,6 +125,7 @@ def library():
             lib.lbm_slab_pack.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
             lib.lbm_slab_unpack.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
             lib.lbm_slab_sums.argtypes = [_VP, P(_D)]
+            lib.lbm_slab_step_part.argtypes = [_VP, ctypes.c_int]
             lib.lbm_measure_fp64_rate.argtypes = [P(_D), P(_D)]
             lib.lbm_batch_create.argtypes = [ctypes.c_int, P(_VP), P(_VP)]
             lib.lbm_batch_set_stream.argtypes = [_VP, _VP]
@@ -139,7 +140,7 @@ def library():
             lib.lbm_batch_destroy.argtypes = [_VP]
             for name in ("lbm_create", "lbm_set_stream", "lbm_set_fields", "lbm_step", "lbm_get_fields",
                          "lbm_get_diagnostics", "lbm_save_state", "lbm_load_state", "lbm_set_tile", "lbm_set_staging",
-                         "lbm_measure_fp64_rate", "lbm_slab_create", "lbm_slab_geometry", "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_sums",
+                         "lbm_measure_fp64_rate", "lbm_slab_create", "lbm_slab_geometry", "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_sums", "lbm_slab_step_part",
                          "lbm_batch_create", "lbm_batch_set_stream", "lbm_batch_set_plan", "lbm_batch_get_plan",
                          "lbm_batch_step", "lbm_batch_sync", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_adjoint_fl_loss"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -205,6 +206,13 @@ def lbm_slab_pack(h, side, phase, msg):
 
 def lbm_slab_unpack(h, side, phase, msg):
     return _check(library().lbm_slab_unpack(h, int(side), int(phase), _ptr(msg)), h)
+
+
+LBM_SLAB_INNER, LBM_SLAB_EDGE = 1, 2
+
+
+def lbm_slab_step_part(h, part):
+    return _check(library().lbm_slab_step_part(h, int(part)), h)
 
 
 def lbm_slab_sums(h, N):
@@ -471,6 +479,15 @@ class SlabSolver(Solver):
         """The band's own rows of a field dict from fields() / fields_numpy()."""
         lo, hi = self.ghost_below, self.ny_local - self.ghost_above
         return {k: v[..., lo:hi, :] for k, v in F.items()}
+
+    def step_part(self, part):
+        """Half of one step: LBM_SLAB_INNER, then LBM_SLAB_EDGE (which completes it)."""
+        lbm_slab_step_part(self.h, part)
+        return self
+
+    def set_stream(self, stream):
+        """Queue the handle's later work on `stream` (a torch.cuda.Stream)."""
+        lbm_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream))
 
     def pack(self, side, phase, msg):
         lbm_slab_pack(self.h, side, phase, msg)

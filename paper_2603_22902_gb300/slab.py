@@ -18,10 +18,19 @@ Two transports:
     gloo on CPU for the tests); remote messages land in local buffers.
 The diagnostics sums of the bands combine by a sum of the N volumes, the N solid
 volumes and the non-finite counts and a maximum of the deviation max |sum phi - 1|.
+
+Overlap (step(n, overlap=True)): a band's step splits into its inner tile rows, which
+neither read nor write the rows the exchange touches, and its edge rows
+(lbm_slab_step_part).  Per step: the inner rows of every band, then the exchange of the
+previous step, then the edge rows; with `streams=(compute, exchange)` the exchange runs
+on the second stream, after an event recorded behind the previous edge part, while the
+inner part runs on the first, which waits for the exchange before the edge part.  The
+last step's exchange follows the loop, so the bands end in the state of step(n).
 """
 from __future__ import annotations
 
 YMIN, YMAX = 2, 3
+INNER, EDGE = 1, 2      # the parts of lbm_slab_step_part
 
 
 def split_rows(ny: int, nbands: int):
@@ -51,6 +60,41 @@ def combine_sums(parts, N):
     return out
 
 
+def _exchange_after(bands, exchange, streams, ev_edge):
+    """One exchange; with streams, on the exchange stream after ev_edge, and the compute
+    stream made to wait for it."""
+    if streams is None:
+        exchange()
+        return
+    import torch
+    compute, xs = streams
+    xs.wait_event(ev_edge)
+    for b in bands:
+        b.set_stream(xs)
+    with torch.cuda.stream(xs):
+        exchange()
+    for b in bands:
+        b.set_stream(compute)
+    compute.wait_event(xs.record_event())
+
+
+def overlapped_steps(bands, exchange, n, streams=None):
+    """n steps of the bands with each exchange placed between the inner and the edge part
+    of the next step (see the module's description); ends with the last step's exchange."""
+    ev_edge = None
+    for t in range(n):
+        for b in bands:
+            b.step_part(INNER)
+        if t > 0:
+            _exchange_after(bands, exchange, streams, ev_edge)
+        for b in bands:
+            b.step_part(EDGE)
+        if streams is not None:
+            ev_edge = streams[0].record_event()
+    if n > 0:
+        _exchange_after(bands, exchange, streams, ev_edge)
+
+
 class LocalExchange:
     """Bands of one lattice in one process.  `bands` are objects with step(n),
     pack(side, phase, msg), unpack(side, phase, msg) and msg_bytes[phase] (SlabSolver);
@@ -76,7 +120,10 @@ class LocalExchange:
             for k, side, r, rside in self.links:
                 self.bands[r].unpack(rside, ph, self.msg[(k, side, ph)])
 
-    def step(self, n=1):
+    def step(self, n=1, overlap=False, streams=None):
+        if overlap:
+            overlapped_steps(self.bands, self.exchange, n, streams)
+            return
         for _ in range(n):
             for b in self.bands:
                 b.step(1)
@@ -139,7 +186,10 @@ class DistExchange:
             for side in sides:
                 b.unpack(side, ph, self.recv[(side, ph)])
 
-    def step(self, n=1):
+    def step(self, n=1, overlap=False, streams=None):
+        if overlap:
+            overlapped_steps([self.band], self.exchange, n, streams)
+            return
         for _ in range(n):
             self.band.step(1)
             self.exchange()

@@ -7,7 +7,9 @@ N = 2, 3, 4, FP64, double words and FP16 storage; the bands' diagnostics sums, c
 must equal the single handle's diagnostics; one run is checked against the CPU oracle
 to the parity bar; and two processes, one band each on the same GPU, exchanging their
 messages through torch.distributed (gloo, host buffers) as ranks of a multi-GPU run do
-(NCCL, device buffers), step exactly like the single handle too."""
+(NCCL, device buffers), step exactly like the single handle too.  The overlapped
+schedule (each step split into inner and edge tile rows, the exchange on a second stream
+between them) must equal the plain one bit for bit."""
 import os
 import socket
 
@@ -58,12 +60,16 @@ CASES = {
 }
 
 
-def run_bands(L, case, bands, steps, precision="fp64"):
+def run_bands(L, case, bands, steps, precision="fp64", overlap=False):
     import torch
     solvers = [L.SlabSolver(case, y0, y1, precision=precision).set_fields() for y0, y1 in bands]
     ex = LocalExchange(solvers, case.bc[2] == W.PERIODIC,
                        alloc=lambda n: torch.empty(n, dtype=torch.uint8, device="cuda"))
-    ex.step(steps)
+    if overlap:
+        # the exchange on a second stream, between the inner and the edge part of each step
+        ex.step(steps, overlap=True, streams=(torch.cuda.current_stream(), torch.cuda.Stream()))
+    else:
+        ex.step(steps)
     parts = [s.own(s.fields_numpy()) for s in solvers]
     F = {k: np.concatenate([P[k] for P in parts], axis=-2) for k in FIELDS}
     sums = ex.sums(case.N)
@@ -180,3 +186,46 @@ def test_bands_on_two_ranks_equal_the_single_lattice(lbm):
         for p in range(case.N):
             assert abs(sums["mass"][p] - d["mass"][p]) <= 1e-12 * max(1.0, d["mass"][p])
         assert sums["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("name", ["sessile_walls_2", "periodic_drop_3", "compound_walls_3", "N4_walls_4"])
+@pytest.mark.parametrize("precision", ["fp64", "fp16s"])
+def test_overlapped_schedule_equals_plain(lbm, name, precision):
+    # every step split into its inner tile rows and its edge rows (lbm_slab_step_part),
+    # with the previous step's exchange on a second stream between the two: each
+    # destination slot is written by one cell either way, so the bands' rows must equal the
+    # plain schedule's bit for bit
+    maker, bands = CASES[name]
+    case = maker()
+    bands = bands or split_rows(case.ny, int(name[-1]))
+    A, sa = run_bands(lbm, case, bands, 60, precision)
+    B, sb = run_bands(lbm, case, bands, 60, precision, overlap=True)
+    for k in FIELDS:
+        assert np.array_equal(A[k], B[k]), (name, precision, k, float(np.abs(A[k] - B[k]).max()))
+    assert sa == sb
+
+
+def test_step_part_order_is_checked(lbm):
+    case = W.sessile_drop(n=96, R=28.0, ny=80, theta=70.0)
+    s = lbm.SlabSolver(case, 0, 40).set_fields()
+    with pytest.raises(lbm.LBMError) as e:
+        s.step_part(lbm.LBM_SLAB_EDGE)          # edge rows before the inner rows
+    assert e.value.code == lbm.LBM_ESTATE
+    s.step_part(lbm.LBM_SLAB_INNER)
+    with pytest.raises(lbm.LBMError) as e:
+        s.step_part(lbm.LBM_SLAB_INNER)         # the inner rows twice
+    assert e.value.code == lbm.LBM_ESTATE
+    with pytest.raises(lbm.LBMError) as e:
+        s.step(1)                               # a whole step in between
+    assert e.value.code == lbm.LBM_ESTATE
+    s.step_part(lbm.LBM_SLAB_EDGE)
+    assert s.steps == 1
+    with pytest.raises(lbm.LBMError) as e:
+        s.step_part(3)
+    assert e.value.code == lbm.LBM_EINVAL
+    s.close()
+    whole = lbm.Solver(case).set_fields()
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_slab_step_part(whole.h, lbm.LBM_SLAB_INNER)   # not a slab handle
+    assert e.value.code == lbm.LBM_EINVAL
+    whole.close()

@@ -35,6 +35,7 @@ class FakeBand:
     def __init__(self, rank):
         self.rank = rank
         self.n = 0
+        self.log = []
         self.rows = {k: np.zeros(W) for k in ("ghost_below", "first", "last", "ghost_above")}
         self.msg_bytes = {1: 8 * W, 2: 8 * W}
 
@@ -45,6 +46,12 @@ class FakeBand:
         r["ghost_below"][:] = tag(self.rank, PUSH_DOWN, self.n)
         r["first"][:] = tag(self.rank, FIRST, self.n)
         r["last"][:] = tag(self.rank, LAST, self.n)
+
+    def step_part(self, part):
+        # the inner part touches none of the rows here; the edge part completes the step
+        self.log.append(("inner" if part == S.INNER else "edge", self.n + 1))
+        if part == S.EDGE:
+            self.step(1)
 
     def pack(self, side, phase, msg):
         if phase == 1:
@@ -90,16 +97,28 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _worker(rank, world, port, periodic, q):
+def _worker(rank, world, port, periodic, q, overlap=False):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     import torch.distributed as dist
     dist.init_process_group("gloo", rank=rank, world_size=world)
     band = FakeBand(rank)
     ex = S.DistExchange(band, periodic, alloc=lambda n: torch.zeros(n // 8, dtype=torch.float64))
+    plain_exchange = ex.exchange
+
+    def logged_exchange():
+        band.log.append(("exchange", band.n))
+        plain_exchange()
+
+    ex.exchange = logged_exchange
     out = []
-    for _ in range(3):
-        ex.step(1)
-        out.append({k: v.copy() for k, v in band.rows.items()})
+    if overlap:
+        ex.step(3, overlap=True)
+        out = [None, None, {k: v.copy() for k, v in band.rows.items()}]
+    else:
+        for _ in range(3):
+            ex.step(1)
+            out.append({k: v.copy() for k, v in band.rows.items()})
+    out.append(band.log)
     sums = ex.sums(2)
     dist.destroy_process_group()
     q.put((rank, out, sums))
@@ -120,7 +139,12 @@ def test_exchange_order_and_sums_on_two_gloo_ranks(periodic):
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for n, step in enumerate(range(1, 4)):
+    check_rows(res, periodic, range(3))
+
+
+def check_rows(res, periodic, which):
+    for n in which:
+        step = n + 1
         lo, hi = res[0][0][n], res[1][0][n]
         # phase 1: the rows pushed across the 0|1 cut arrive in the boundary rows
         assert np.array_equal(hi["first"], tag(0, PUSH_UP, step))
@@ -143,3 +167,27 @@ def test_exchange_order_and_sums_on_two_gloo_ranks(periodic):
         got = res[r][1]
         assert got["mass"] == expect["mass"] and got["solid"] == expect["solid"]
         assert got["max_sum_dev"] == expect["max_sum_dev"] and got["nonfinite"] == expect["nonfinite"]
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_overlapped_schedule_on_two_gloo_ranks(periodic):
+    # step(3, overlap=True): per step the inner part, the previous step's exchange, the edge
+    # part; the last exchange after the loop.  The rows end as after three plain steps.
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, periodic, q, True)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in procs:
+        r, out, sums = q.get(timeout=120)
+        res[r] = (out, sums)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    check_rows(res, periodic, [2])
+    for r in (0, 1):
+        log = res[r][0][3]
+        assert log == [("inner", 1), ("edge", 1), ("inner", 2), ("exchange", 1), ("edge", 2),
+                       ("inner", 3), ("exchange", 2), ("edge", 3), ("exchange", 3)], log
