@@ -195,6 +195,29 @@ def test_staged_batch_equals_per_step_and_single_runs(lbm, prec):
         assert e <= 2e-2, (cases[k].name, e)
 
 
+def test_staged_batch_n3(lbm):
+    # N = 3 cases in the staged form (three blocks per SM): against the per-step form and
+    # the single runs, within one unit of the 16-bit format like the N = 2 batch
+    cases = [W.liquid_lens(nx=64, ny=48, R=10.0), W.compound_drop(n=128, R_core=12.0, R_shell=24.0),
+             W.compound_drop(n=96, R_core=10.0, R_shell=20.0, ny=72)]
+    ref = singles(lbm, cases, 30, "fp16s")
+    out = {}
+    for mode in ("per_step", "staged"):
+        solvers = [lbm.Solver(c, precision="fp16s").set_fields() for c in cases]
+        b = lbm.Batch(solvers).set_plan(mode=mode, tiles=[(32, 8)] * lbm.BATCH_CLASSES)
+        b.step(15).step(15).sync()
+        assert b.plan.as_dict()["mode"] == mode
+        out[mode] = [s.fields_numpy() for s in solvers]
+        b.close()
+        for s in solvers:
+            s.close()
+    for k, c in enumerate(cases):
+        e1 = max_err(out["per_step"][k], out["staged"][k])
+        e2 = max_err(out["staged"][k], ref[k])
+        print(c.name, "staged vs per-step", e1, "vs single", e2)
+        assert e1 <= 2e-2 and e2 <= 2e-2, (c.name, e1, e2)
+
+
 def test_staged_batch_autotune_and_fallback(lbm):
     # the autotuner considers the staged form where a group allows it; a 32x8 group with
     # a case whose nx is not a multiple of 8 runs the per-step form in the staged mode
