@@ -47,6 +47,8 @@ CASES = {
     "sessile_cap_160x64_walls": lambda: W.sessile_cap(160, 64, 18.0, theta=110.0, ste=0.3, T_wall=-1.5),
     "film_16x256": lambda: W.film(nx=16, ny=256),
     "sessile_72x60_ragged": lambda: W.sessile_drop(n=72, R=20.0, ny=60, theta=80.0),
+    "periodic_8x5_tiny": lambda: W.perturbed(W.periodic_drop(n=8, R=2.0, ny=5, rho_gas=0.5), seed=2),
+    "film_16x3_minimal": lambda: W.film(nx=16, ny=3, h0=1.5),
 }
 CASES_N3 = {
     "lens_64x48_N3": lambda: W.liquid_lens(nx=64, ny=48, R=10.0),
