@@ -6,7 +6,7 @@ A lattice of ny rows is cut into bands; band k holds rows [y0_k, y1_k).  After e
 step, each cut is crossed by two messages per direction (phase 1: the populations pushed
 across it; phase 2: the boundary row's stencil inputs).  Per phase the order is fixed:
 every band packs all its cut sides, the messages travel, every band unpacks.  The
-transfers of one phase go in two rounds, first every band's y-max message to the band
+transfers of one phase go in two passes, first every band's y-max message to the band
 above (unpacked there on its y-min side), then every band's y-min message to the band
 below, so that two ranks that are each other's upper and lower neighbour (two bands of a
 periodic lattice) post their sends and receives in the same order.
@@ -154,8 +154,8 @@ class DistExchange:
             self.host_recv = {k: host_alloc(band.msg_bytes[k[1]]) for k in self.recv}
 
     def _transfer(self, ph):
-        """Round 1: y-max messages go up (received on the y-min side); round 2: y-min
-        messages go down (received on the y-max side).  Each round is one batch of
+        """Pass 1: y-max messages go up (received on the y-min side); pass 2: y-min
+        messages go down (received on the y-max side).  Each pass is one batch of
         point-to-point operations, posted in the same order on every rank."""
         d = self.dist
         staged = self.host_send is not None

@@ -141,7 +141,7 @@ def test_autograd_function(lbm):
     (2.0 * loss).backward()
     case = build(**THETA)
     g = run_adjoint(case, target, nsteps, 20)
-    assert float(loss) == g.loss
+    assert float(loss.detach()) == g.loss
     assert np.allclose(theta.grad.numpy(), 2.0 * theta_gradient(case, g), rtol=0, atol=0)
 
 
