@@ -64,7 +64,7 @@ extern "C" {
 #define LBM_BF16S 3 /* BF16 storage of shifted populations, FP32 arithmetic */
 #define LBM_DF64 4  /* double-word (FP32 pair, ~48-bit) storage and arithmetic on the FP32
                        pipes, the enthalpy map in FP64 where it decides f_l; held to the
-                       FP64 parity bar; 32x8 tiles only, no batch form */
+                       FP64 parity bar; 32x8 tiles only (batches too) */
 
 #define LBM_HOST 0
 #define LBM_DEVICE 1
@@ -399,7 +399,8 @@ typedef struct {
 } lbm_batch_plan;
 
 /* Build a batch over ncases handles, owned by the caller.
- * - All handles live on the current device and share N and the precision policy.
+ * - All handles live on the current device and share N and the precision policy
+ *   (LBM_DF64 batches use 32x8 tiles only: lbm_batch_set_plan refuses other shapes).
  * - Every handle must have been given fields (lbm_set_fields).
  * - The initial plan is persistent, 32x8 tiles for every class, all blocks that fit.
  * - Errors: LBM_EINVAL for mixed N or precision, a NULL or repeated handle, or

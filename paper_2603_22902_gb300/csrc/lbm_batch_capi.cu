@@ -378,6 +378,8 @@ static int apply_plan(lbm_batch* b, const lbm_batch_plan* p)
     for (int k = 0; k < LBM_BATCH_CLASSES; ++k) {
         kinds[k] = kind_of_shape(p->tile[k][0], p->tile[k][1]);
         if (kinds[k] < 0) return bfail(b, LBM_EINVAL, "batch tile shapes are 32x8, 64x4 or 16x16");
+        if (b->precision == LBM_DF64 && KIND_TILE[kinds[k]] != TILE_32x8)
+            return bfail(b, LBM_EINVAL, "the LBM_DF64 policy is compiled for the 32x8 tile only");
     }
     bool retable = false;
     for (int k = 0; k < LBM_BATCH_CLASSES; ++k) retable = retable || kinds[k] != b->class_kind[k];
@@ -420,8 +422,6 @@ int lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** out)
         if (cases[c]->N != cases[0]->N) return bfail(nullptr, LBM_EINVAL, "batch cases must share N");
         if (cases[c]->precision != cases[0]->precision)
             return bfail(nullptr, LBM_EINVAL, "batch cases must share the precision policy");
-        if (cases[c]->precision == LBM_DF64)
-            return bfail(nullptr, LBM_EINVAL, "the LBM_DF64 policy has no batch form");
         if (cases[c]->device != cases[0]->device) return bfail(nullptr, LBM_EINVAL, "batch cases must share a device");
         if (!cases[c]->ready) return bfail(nullptr, LBM_ESTATE, "a batch case has no fields (lbm_set_fields)");
     }
@@ -596,7 +596,7 @@ int lbm_batch_autotune(lbm_batch* b, int trial_steps, lbm_batch_plan* best)
         rc = consider(p);
     }
     for (int k = 0; k < LBM_BATCH_CLASSES && rc == LBM_OK; ++k) {
-        if (!present[k]) continue;
+        if (!present[k] || b->precision == LBM_DF64) continue;   // double words: 32x8 only
         for (int kind = 0; kind < NKIND && rc == LBM_OK; ++kind) {
             if (KIND_TX[kind] == cur.tile[k][0] && KIND_TY[kind] == cur.tile[k][1]) continue;
             lbm_batch_plan p = cur;

@@ -26,7 +26,7 @@ static cudaError_t launch_fused_t(const KParams& P, const void* pin, void* pout,
 }
 
 // The double-word policy is compiled for the 32 x 8 tile only (each shape of its kernel
-// adds much code); lbm_set_tile refuses other shapes for it, and it has no batch form.
+// adds much code); lbm_set_tile and the batch plans refuse other shapes for it.
 template <class Pr>
 constexpr bool single_shape() { return std::is_same<Pr, PrecDF64>::value; }
 
@@ -120,7 +120,8 @@ template <int N, class Pr>
 cudaError_t launch_batch_persistent(const BatchTable& T, int kind, int nsteps, int blocks, cudaStream_t st)
 {
     if constexpr (single_shape<Pr>()) {
-        return cudaErrorNotSupported;
+        if (kind != TILE_32x8) return cudaErrorNotSupported;
+        return launch_batch_persistent_t<N, 32, 8, Pr>(T, nsteps, blocks, st);
     } else {
         switch (kind) {
             case TILE_64x4: return launch_batch_persistent_t<N, 64, 4, Pr>(T, nsteps, blocks, st);
@@ -134,7 +135,8 @@ template <int N, class Pr>
 cudaError_t batch_blocks_per_sm(int kind, int* out)
 {
     if constexpr (single_shape<Pr>()) {
-        return cudaErrorNotSupported;
+        if (kind != TILE_32x8) return cudaErrorNotSupported;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_persistent_kernel<N, 32, 8, Pr>, BATCH_NT, 0);
     } else {
         switch (kind) {
             case TILE_64x4:
@@ -152,7 +154,9 @@ template <int N, class Pr>
 cudaError_t launch_batch_step(const BatchTable& T, int kind, int s, cudaStream_t st)
 {
     if constexpr (single_shape<Pr>()) {
-        return cudaErrorNotSupported;
+        if (kind != TILE_32x8) return cudaErrorNotSupported;
+        batch_step_kernel<N, 32, 8, Pr><<<T.total_tiles, BATCH_NT, 0, st>>>(T, s);
+        return cudaGetLastError();
     } else {
         switch (kind) {
             case TILE_64x4: batch_step_kernel<N, 64, 4, Pr><<<T.total_tiles, BATCH_NT, 0, st>>>(T, s); break;

@@ -5,7 +5,7 @@ one case through the batch must match the CPU oracle to the 1e-10 parity bar.  B
 launch forms, all three tile shapes, odd step counts in both forms (each call is replayed
 as a captured graph; the persistent launch flips its own parity, the per-step form ends an
 odd call with a parity-flip kernel), members stepped alone between batch steps, and the
-autotuner's restoration of the state are covered.  The staged form (16-bit storage, N = 2,
+autotuner's restoration of the state are covered, for FP64 and for double words (32x8 tiles).  The staged form (16-bit storage, N = 2,
 32x8 tiles) runs the staged step's arithmetic: its cases must match the per-step form's
 and the single runs' to one unit of the 16-bit format, like the per-step form."""
 import numpy as np
@@ -149,6 +149,35 @@ def test_reduced_precision_batch_matches_single_runs(lbm, prec):
     for s, c, R in zip(solvers, cases, ref):
         e = max_err(s.fields_numpy(), R)
         assert e <= bound, (c.name, prec, e)
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+@pytest.mark.parametrize("mode", ["persistent", "per_step"])
+def test_double_word_batch(lbm, mode):
+    # the double-word policy in both batch forms (32x8 tiles): every case as its single run
+    # to rounding, one case against the oracle at the parity bar; other tile shapes refused
+    cases = W.small_batch()
+    steps = 60
+    ref = singles(lbm, cases, steps, "df64")
+    solvers = [lbm.Solver(c, precision="df64").set_fields() for c in cases]
+    b = lbm.Batch(solvers).set_plan(mode=mode, tiles=[(32, 8)] * lbm.BATCH_CLASSES)
+    b.step(steps).sync()
+    for s, c, R in zip(solvers, cases, ref):
+        e = max_err(s.fields_numpy(), R)
+        assert e <= 1e-12, (c.name, mode, e)
+    b.step(140).sync()
+    O = oracle.Oracle(cases[0]).step(200).fields()
+    e = max_err(solvers[0].fields_numpy(), O)
+    assert e <= 1e-10, (cases[0].name, e)
+    p = b.plan
+    p.tile[0][0], p.tile[0][1] = 64, 4
+    with pytest.raises(lbm.LBMError) as err:
+        lbm.lbm_batch_set_plan(b.b, p)
+    assert err.value.code == lbm.LBM_EINVAL
+    plan = b.autotune(trial_steps=4)
+    assert all(tuple(t) == (32, 8) for t in plan["tile"]), plan
     b.close()
     for s in solvers:
         s.close()
