@@ -134,9 +134,13 @@ def test_df64_interface_limits(lbm):
     assert e.value.code == lbm.LBM_EINVAL
     lbm.lbm_set_tile(s.h, 32, 8)
     s.set_fields()
+    b = lbm.Batch([s])                         # batches: 32x8 tiles only
+    p = b.plan
+    p.tile[0][0], p.tile[0][1] = 16, 16
     with pytest.raises(lbm.LBMError) as e:
-        lbm.Batch([s])
+        lbm.lbm_batch_set_plan(b.b, p)
     assert e.value.code == lbm.LBM_EINVAL
+    b.close()
     s.close()
 
 
